@@ -1,0 +1,240 @@
+/*
+ * meshloop -- C ABI of the GB300 (sm_103a) library for locality-optimised
+ * indirect-increment mesh loops, after Sulyok, Balogh, Reguly and Mudalige,
+ * "Locality Optimized Unstructured Mesh Algorithms on GPUs" (2018).
+ *
+ * Model (Sec. 1.1.1): a mesh is a collection of sets; a map gives, for every
+ * element of a from-set, a fixed number (the arity) of indices into a to-set;
+ * data live on sets.  A loop runs over a from-set, reads data directly on it
+ * or through one level of maps, and may INCREMENT data through a map.  The
+ * result must not depend on iteration order, up to rounding.
+ *
+ * Execution (Sec. 2.2, Algorithm 1): iterations are grouped into blocks of at
+ * most S (one CUDA thread block each).  Each block stages the to-set data it
+ * touches (its "footprint") in shared memory, computes every iteration from
+ * shared memory, applies its increments to shared memory one thread colour at
+ * a time, and writes each footprint point back to global memory once.
+ * Blocks of one block colour never share a written point, so a launch per
+ * block colour needs no atomics (two-layer or hierarchical colouring).
+ * Baselines from Sec. 2.1: global colouring (one launch per iteration
+ * colour, direct global read-modify-write) and atomics.
+ *
+ * Planning (Sec. 2.3): optional reverse Cuthill-McKee reordering (a
+ * bandwidth-reducing BFS ordering in the spirit of GPS), partitioning of the
+ * iterations into compact blocks of at most S' = floor(S / l) (Eq. 1),
+ * data-point reordering by the set of accessing blocks, first-fit block and
+ * thread colouring.
+ *
+ * Conventions used by every call below:
+ *  - Return value: MP_OK (0) or a negative MP_E* code; mp_error_string()
+ *    names it.  A failing call leaves its outputs unspecified but frees
+ *    whatever it allocated.
+ *  - Host pointers are read during the call only; the caller keeps them.
+ *  - Data pointers passed to loop_* calls are DEVICE pointers of the
+ *    current CUDA device, owned by the caller, 16-byte aligned, in PLAN
+ *    numbering (mesh_plan_perm gives the permutations).  Data are stored
+ *    either array-of-structures (x[node][2]) or structure-of-arrays
+ *    (x[2][node]) as chosen by mp_plan_opts.layout; dtype selects double or
+ *    float storage and arithmetic.
+ *  - Increments are "+=": the caller zeroes an increment target first.
+ *  - Loop calls are asynchronous on the given stream (0 = legacy default)
+ *    and never synchronise the device.  The first loop call on a plan
+ *    uploads its tables (cudaMalloc + cudaMemcpy, synchronous); call
+ *    mesh_plan_upload() first when the loop will be captured in a graph.
+ */
+#ifndef MESHLOOP_H
+#define MESHLOOP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define MP_OK 0
+#define MP_EINVAL (-1)     /* null or misaligned pointer, bad arity/size/option        */
+#define MP_EMAPRANGE (-2)  /* a map index is outside [0, to_size)                      */
+#define MP_ECOLORS (-3)    /* more than MP_MAX_BLOCK_COLORS block colours (Sec. 3.1.5)  */
+#define MP_ESMEM (-4)      /* a block footprint exceeds shared memory (Sec. 3.1.5)      */
+#define MP_ECUDA (-5)      /* a CUDA runtime call failed                               */
+#define MP_ETIMEOUT (-6)   /* a bounded device-side wait gave up                       */
+#define MP_ENOMEM (-7)     /* host allocation failed                                   */
+#define MP_EPLAN (-8)      /* plan does not fit the loop (maps, colouring, layout)     */
+#define MP_EIO (-9)        /* plan file could not be read or written                   */
+
+#define MP_MAX_BLOCK_COLORS 256  /* limit of the paper's library, Sec. 3.1.5        */
+#define MP_MAX_THREAD_COLORS 64
+#define MP_MAX_MAPS 4
+#define MP_MAX_TOSETS 2
+
+/* ------------------------------------------------------------- options */
+enum { MP_REORDER_NONE = 0, MP_REORDER_RCM = 1, MP_REORDER_PARTITION = 2 };
+enum { MP_COLOR_HIER = 0, MP_COLOR_GLOBAL = 1, MP_COLOR_ATOMIC = 2 };
+enum { MP_LAYOUT_AOS = 0, MP_LAYOUT_SOA = 1 };
+enum { MP_F64 = 0, MP_F32 = 1 };
+
+/* One map of the loop: from the loop's iteration set (set id 0) to the
+ * caller's set `to_set` (ids >= 1; maps with the same id share a to-set).
+ * idx is host memory, from_size x arity, row-major, int32.               */
+typedef struct {
+    int32_t to_set;
+    int32_t arity;     /* 1..8                                            */
+    int64_t to_size;   /* number of points in the to-set                  */
+    const int32_t *idx;
+    int32_t written;   /* 1: the loop increments data through this map   */
+    int32_t pad_;
+} mp_map;
+
+/* Planner options (Sec. 2.3 tuning parameters). */
+typedef struct {
+    int32_t block_size;  /* S: launched threads per block, 32..1024, multiple of 32  */
+    int32_t reorder;     /* MP_REORDER_*                                             */
+    int32_t coloring;    /* MP_COLOR_*                                               */
+    int32_t layout;      /* MP_LAYOUT_*                                              */
+    double imbalance;    /* l of Eq. 1 (default 1.001); S' = floor(S / l)            */
+    double eps;          /* epsilon of Eq. 2 (default 0), reported through l'        */
+    int32_t primary_map; /* map whose to-set is RCM-ordered; -1 = first written map  */
+    int32_t data_reorder;/* 1: reorder to-set points by accessing blocks (Sec. 2.3.2);
+                            -1: default (on with MP_REORDER_PARTITION)              */
+} mp_plan_opts;
+
+/* Fill opts with defaults: S = 512, PARTITION, HIER, AOS, l = 1.001. */
+void mp_plan_opts_default(mp_plan_opts *opts);
+
+typedef struct mp_plan mp_plan;
+
+/* Plan statistics (Sec. 3.1's counters). reuse[t] = accesses to to-set t
+ * through staged maps / staged footprint points, summed over blocks (the
+ * paper's data reuse factor, Sec. 3.1).                                  */
+typedef struct {
+    int64_t from_size;
+    int32_t nblocks;
+    int32_t nblock_colors;     /* block colours (HIER) or iteration colours (GLOBAL)  */
+    int32_t max_thread_colors;
+    int32_t block_size;        /* S                                                  */
+    int32_t sprime;            /* S' of Eq. 1                                         */
+    int32_t ntosets;
+    double lprime;             /* l' of Eq. 2                                         */
+    double mean_thread_colors;
+    double reuse[MP_MAX_TOSETS];
+    double reuse_all;          /* over all staged maps                               */
+    int64_t footprint_total[MP_MAX_TOSETS];
+    int32_t footprint_max[MP_MAX_TOSETS];
+    int32_t to_set_id[MP_MAX_TOSETS];
+    int64_t plan_bytes;        /* device bytes of the plan tables                     */
+    double seconds_total, seconds_reorder, seconds_partition, seconds_color;
+} mp_plan_stats;
+
+/* Build a plan for a loop over a from-set of from_size iterations with the
+ * given maps (Sec. 2.3; reordering, partitioning, colouring).  Host only;
+ * touches no GPU.  *out is owned by the caller: mesh_plan_destroy().
+ * Errors: MP_EINVAL, MP_EMAPRANGE, MP_ECOLORS, MP_ENOMEM.                */
+int mesh_plan_build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_opts *opts,
+                    mp_plan **out);
+void mesh_plan_destroy(mp_plan *plan);
+int mesh_plan_query(const mp_plan *plan, mp_plan_stats *stats);
+
+/* new_to_old permutation of set `set_id` (0 = the from-set, else a to-set
+ * id of the maps): new_to_old[new] = old, length = the set's size.        */
+int mesh_plan_perm(const mp_plan *plan, int32_t set_id, int32_t *new_to_old);
+
+/* Copy one host plan table into out (capacity `cap` elements of the
+ * table's type; *count receives the length).  Tables:
+ *   MP_TAB_BLOCK_OFFSETS  int32[nblocks+1]  iteration range of each block
+ *   MP_TAB_COLOR_OFFSETS  int32[ncolors+1]  block (HIER) or iteration (GLOBAL)
+ *                                           range of each colour
+ *   MP_TAB_BLOCK_COLOR    int32[nblocks]
+ *   MP_TAB_THREAD_COLOR   int32[from_size]  thread colour of each iteration
+ *   MP_TAB_MAP            int32[from_size*arity] map `arg` in plan numbering
+ * Iterations are in plan numbering.                                       */
+enum { MP_TAB_BLOCK_OFFSETS = 0, MP_TAB_COLOR_OFFSETS = 1, MP_TAB_BLOCK_COLOR = 2,
+       MP_TAB_THREAD_COLOR = 3, MP_TAB_MAP = 4 };
+int mesh_plan_table(const mp_plan *plan, int32_t table, int32_t arg, int32_t *out, int64_t cap,
+                    int64_t *count);
+
+/* Renumber a map given new_to_old permutations of its from-set and to-set
+ * (either may be NULL for identity) and sort nothing else:
+ *   out[i][k] = old_to_new_to[idx[from_perm[i]][k]].                     */
+int mesh_map_renumber(const int32_t *idx, int64_t from_size, int32_t arity, const int32_t *from_perm,
+                      const int32_t *to_perm, int64_t to_size, int32_t *out);
+
+/* Copy the plan's tables to the current device (synchronous).  Idempotent.*/
+int mesh_plan_upload(mp_plan *plan);
+
+/* Serialise / restore a plan (reordering is a reusable one-off, Sec. 2.3.2).*/
+int mesh_plan_save(const mp_plan *plan, const char *path);
+int mesh_plan_load(const char *path, mp_plan **out);
+
+/* --------------------------------------------------------------- loops */
+/* Airfoil-style flux loop res_calc (Sec. 3.1.1): over interior edges,
+ * reading x (2 per node) on 2 nodes and q (4), adt (1) on 2 cells, and
+ * incrementing res (4 per cell) on the 2 cells: res[c1] += f, res[c2] -= f
+ * with the central flux plus scalar dissipation
+ *   f = (F(q1).n + F(q2).n)/2 + eps (adt1 + adt2)/2 (q1 - q2),
+ *   n = (y_a - y_b, x_b - x_a), F.n the 2D Euler normal flux, gamma = gam.
+ * The plan must have maps {edge->node (arity 2, read), edge->cell (arity 2,
+ * written)} in this order.  The colouring of the plan selects the variant:
+ * HIER (staged two-layer, the product), GLOBAL or ATOMIC.
+ * x: [nodes][2], q: [cells][4], adt: [cells], res: [cells][4] (AoS; SoA
+ * transposes each).  stream is a cudaStream_t.                          */
+int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
+                  void *res, double gam, double eps, void *stream);
+
+/* Far-field boundary flux bres_calc over boundary edges: with
+ * q_b = (q_c + qinf)/2,  res[c] += F(q_b).n + eps adt_c (q_c - qinf).
+ * Plan maps {bedge->node (2, read), bedge->cell (1, written)}; colouring
+ * GLOBAL or ATOMIC or HIER.  qinf: 4 host doubles.                       */
+int loop_bres_calc(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
+                   void *res, const double *qinf, double gam, double eps, void *stream);
+
+/* adt_calc over cells (read-only indirection through cell->node[4], corners
+ * counter-clockwise): adt = sum over the 4 sides of
+ *   (|u dy - v dx| + c sqrt(dx^2 + dy^2)) / cfl,  c = sqrt(gam p / rho).
+ * Plan maps {cell->node (4, read)}; any colouring (none is needed).       */
+int loop_adt_calc(const mp_plan *plan, int32_t dtype, const void *x, const void *q, void *adt,
+                  double gam, double cfl, void *stream);
+
+/* save_soln + update, direct loops over ncell cells in the given layout:
+ *   loop_save_soln: qold = q
+ *   loop_update:    d = res/adt (in FP64), q = qold - d, res = 0,
+ *                   *rms_dev (a device double) += sum of d^2 in FP64.
+ * The sum is deterministic (fixed-order two-pass reduction in plan-free
+ * scratch owned by the library; calls on one device must not overlap).  */
+int loop_save_soln(int64_t ncell, int32_t dtype, int32_t layout, const void *q, void *qold,
+                   void *stream);
+int loop_update(int64_t ncell, int32_t dtype, int32_t layout, const void *qold, void *q, void *res,
+                const void *adt, double *rms_dev, void *stream);
+
+/* Hex assembly (Sec. 3.1.4's IntegrateStressForElems access pattern): over
+ * hex8 elements read x, v (3 per node) on 8 nodes and sig (3, direct),
+ * write vol (direct) and increment f (3 per node) on the 8 nodes, with the
+ * one-point hex8 stress force -diag(sig) B_i and Flanagan-Belytschko
+ * hourglass force (coefficient kappa).  Corner order of elem->node:
+ * (-,-,-),(+,-,-),(+,+,-),(-,+,-),(-,-,+),(+,-,+),(+,+,+),(-,+,+).
+ * Plan maps {elem->node (8, written)}.  x, v, f: [nodes][3];
+ * sig: [elems][3]; vol: [elems].                                         */
+int loop_elem_assemble(const mp_plan *plan, int32_t dtype, const void *x, const void *v,
+                       const void *sig, void *f, void *vol, double kappa, void *stream);
+
+/* Adjoint of res_calc with x, q, adt fixed (adt not differentiated):
+ *   q_bar += (d res/d q)^T res_bar,  x_bar += (d res/d x)^T res_bar.
+ * Both maps are written, so the plan has maps {edge->node (2, written),
+ * edge->cell (2, written)}.  FP64 only.                                  */
+int loop_adjoint(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
+                 const void *res_bar, void *q_bar, void *x_bar, double gam, double eps,
+                 void *stream);
+
+/* --------------------------------------------------------------- status */
+const char *mp_error_string(int code);
+/* Reads (and clears) the device error word of the library's bounded waits:
+ * MP_OK or MP_ETIMEOUT.  Synchronises the stream.                       */
+int mp_check_device_status(void *stream);
+/* Library version string. */
+const char *mp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MESHLOOP_H */
