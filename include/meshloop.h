@@ -123,6 +123,7 @@ typedef struct {
     int64_t footprint_total[MP_MAX_TOSETS];
     int32_t footprint_max[MP_MAX_TOSETS];
     int32_t to_set_id[MP_MAX_TOSETS];
+    int64_t to_set_size[MP_MAX_TOSETS];
     int64_t plan_bytes;        /* device bytes of the plan tables                     */
     double seconds_total, seconds_reorder, seconds_partition, seconds_color;
 } mp_plan_stats;
@@ -148,9 +149,18 @@ int mesh_plan_perm(const mp_plan *plan, int32_t set_id, int32_t *new_to_old);
  *   MP_TAB_BLOCK_COLOR    int32[nblocks]
  *   MP_TAB_THREAD_COLOR   int32[from_size]  thread colour of each iteration
  *   MP_TAB_MAP            int32[from_size*arity] map `arg` in plan numbering
+ *   MP_TAB_FOOTPRINT      int32[...]  HIER: all blocks' footprint lists (plan
+ *                                     numbering), to-set slot 0 first
+ *   MP_TAB_FP_START       int32[nblocks*MP_MAX_TOSETS] HIER: offset of each
+ *                                     block's list per slot in MP_TAB_FOOTPRINT
+ *   MP_TAB_FP_COUNT       int32[nblocks*MP_MAX_TOSETS] HIER: list lengths
+ *   MP_TAB_LOCAL_MAP      int32[from_size*stride] HIER: block-local index of
+ *                                     every map slot (maps in order, padded
+ *                                     to stride = 4, 8 or 16 entries)
  * Iterations are in plan numbering.                                       */
 enum { MP_TAB_BLOCK_OFFSETS = 0, MP_TAB_COLOR_OFFSETS = 1, MP_TAB_BLOCK_COLOR = 2,
-       MP_TAB_THREAD_COLOR = 3, MP_TAB_MAP = 4 };
+       MP_TAB_THREAD_COLOR = 3, MP_TAB_MAP = 4, MP_TAB_FOOTPRINT = 5, MP_TAB_FP_START = 6,
+       MP_TAB_FP_COUNT = 7, MP_TAB_LOCAL_MAP = 8 };
 int mesh_plan_table(const mp_plan *plan, int32_t table, int32_t arg, int32_t *out, int64_t cap,
                     int64_t *count);
 
@@ -174,8 +184,9 @@ int mesh_plan_load(const char *path, mp_plan **out);
  * with the central flux plus scalar dissipation
  *   f = (F(q1).n + F(q2).n)/2 + eps (adt1 + adt2)/2 (q1 - q2),
  *   n = (y_a - y_b, x_b - x_a), F.n the 2D Euler normal flux, gamma = gam.
- * The plan must have maps {edge->node (arity 2, read), edge->cell (arity 2,
- * written)} in this order.  The colouring of the plan selects the variant:
+ * The plan must have maps {edge->node (arity 2), edge->cell (arity 2,
+ * written)} in this order; edge->node may be marked written (the adjoint's
+ * plan, so that forward and adjoint share one numbering).  The colouring of the plan selects the variant:
  * HIER (staged two-layer, the product), GLOBAL or ATOMIC.
  * x: [nodes][2], q: [cells][4], adt: [cells], res: [cells][4] (AoS; SoA
  * transposes each).  stream is a cudaStream_t.                          */

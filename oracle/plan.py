@@ -193,18 +193,21 @@ def data_point_order(block_of_item, idx_list, npoints):
 
 # ------------------------------------------------------------------ metrics
 
-def reuse_factor(block_offsets, idx_list):
+def reuse_factor(block_offsets, idx_list, to_sets=None):
     """Accesses to staged points over distinct staged points, summed over
-    blocks (Sec. 3.1's data reuse factor)."""
+    blocks (Sec. 3.1's data reuse factor).  ``to_sets[k]`` names the to-set
+    of ``idx_list[k]`` (maps into one to-set share its points); by default
+    every map has its own to-set."""
+    to_sets = list(range(len(idx_list))) if to_sets is None else to_sets
     acc = 0
     uniq = 0
     for b in range(len(block_offsets) - 1):
         s, e = block_offsets[b], block_offsets[b + 1]
         pts = set()
-        for idx in idx_list:
+        for t, idx in zip(to_sets, idx_list):
             rows = idx[s:e]
             acc += rows.size
-            pts.update(int(p) for p in rows.ravel())
+            pts.update((t, int(p)) for p in rows.ravel())
         uniq += len(pts)
     return acc / max(uniq, 1)
 

@@ -1,0 +1,80 @@
+// Device-side helpers shared by the loop kernels.  Internal.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan_internal.h"
+
+#define MP_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return MP_ECUDA;             \
+    } while (0)
+
+// Largest dynamic shared memory a CTA may opt into on sm_103a (227 KB).
+constexpr int MP_SMEM_LIMIT = 227 * 1024;
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// True when p is 16-byte aligned (vector loads of double2 / float4 rows).
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Data accessor for a dat of DIM components per point in AoS ([n][DIM]) or
+// SoA ([DIM][n]) layout.
+template <typename T, int DIM, bool SOA>
+struct dat {
+    T *p;
+    int64_t n;
+    __device__ __forceinline__ T &at(int64_t i, int k) const { return SOA ? p[k * n + i] : p[i * DIM + k]; }
+};
+
+// Uploads the plan's tables to the current device if not done yet.
+int mp_plan_ensure_device(const mp_plan *plan);
+
+// Library-owned device scratch for deterministic reductions (per device).
+int mp_reduce_scratch(double **partials, int *nparts);
+
+// Sets the max dynamic smem attribute of a kernel once.
+template <typename K>
+inline int mp_allow_smem(K kernel, int bytes)
+{
+    if (bytes > MP_SMEM_LIMIT) return MP_ESMEM;
+    if (bytes > 48 * 1024) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT) != cudaSuccess)
+            return MP_ECUDA;
+    }
+    return MP_OK;
+}
+
+// ------------------------------------------------------------ 2D Euler flux
+// Per-cell primitives staged once per footprint point: velocity (u, v),
+// pressure p = (gam-1)(E - rho |u|^2 / 2) and total enthalpy density H = E + p.
+template <typename T>
+__device__ __forceinline__ void cell_prims(T rho, T ru, T rv, T E, T gm1, T &u, T &v, T &p, T &H)
+{
+    T ri = T(1) / rho;
+    u = ru * ri;
+    v = rv * ri;
+    p = gm1 * (E - T(0.5) * (ru * u + rv * v));
+    H = E + p;
+}
+
+// Edge flux from two cells' conserved states and primitives with the
+// half normal (nxh, nyh) = n / 2:
+//   f = (F(q1).n + F(q2).n)/2 + mu (q1 - q2),  F.n = (rho V, rho u V + p n_x,
+//   rho v V + p n_y, H V),  V = u . n,  mu = eps (adt1 + adt2) / 2.
+template <typename T>
+__device__ __forceinline__ void edge_flux(T nxh, T nyh, T r1, T ru1, T rv1, T E1, T u1, T v1, T p1, T H1, T a1,
+                                          T r2, T ru2, T rv2, T E2, T u2, T v2, T p2, T H2, T a2, T half_eps,
+                                          T f[4])
+{
+    T V1 = u1 * nxh + v1 * nyh;
+    T V2 = u2 * nxh + v2 * nyh;
+    T ps = p1 + p2;
+    T mu = (a1 + a2) * half_eps;
+    f[0] = r1 * V1 + r2 * V2 + mu * (r1 - r2);
+    f[1] = ru1 * V1 + ru2 * V2 + ps * nxh + mu * (ru1 - ru2);
+    f[2] = rv1 * V1 + rv2 * V2 + ps * nyh + mu * (rv1 - rv2);
+    f[3] = H1 * V1 + H2 * V2 + mu * (E1 - E2);
+}

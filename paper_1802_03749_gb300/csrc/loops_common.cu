@@ -1,0 +1,211 @@
+// Plan upload, library scratch and the direct loops of the time step
+// (save_soln, update with the FP64 residual sum).
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+template <typename T>
+int upload(T **dst, const T *src, size_t n, int64_t &bytes)
+{
+    if (n == 0) return MP_OK;
+    MP_CUDA_TRY(cudaMalloc(reinterpret_cast<void **>(dst), n * sizeof(T)));
+    MP_CUDA_TRY(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    bytes += (int64_t)(n * sizeof(T));
+    return MP_OK;
+}
+
+std::mutex g_upload_mu;
+
+}  // namespace
+
+void mp_plan_free_device(mp_plan *P)
+{
+    mp_device_tables &d = P->dev;
+    if (d.device < 0) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != d.device) cudaSetDevice(d.device);
+    cudaFree(d.desc);
+    cudaFree(d.lmap);
+    cudaFree(d.fp);
+    cudaFree(d.tcolor);
+    for (auto &m : d.map) cudaFree(m);
+    if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
+    d = mp_device_tables{};
+}
+
+int mp_plan_ensure_device(const mp_plan *cplan)
+{
+    mp_plan *P = const_cast<mp_plan *>(cplan);
+    std::lock_guard<std::mutex> lk(g_upload_mu);
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    if (P->dev.device == dev) return MP_OK;
+    if (P->dev.device >= 0) mp_plan_free_device(P);
+    mp_device_tables &d = P->dev;
+    int rc = MP_OK;
+    int64_t bytes = 0;
+    if (P->opts.coloring == MP_COLOR_HIER) {
+        if ((rc = upload(&d.desc, P->desc.data(), P->desc.size(), bytes)) != MP_OK) goto fail;
+        if ((rc = upload(&d.lmap, P->lmap.data(), P->lmap.size(), bytes)) != MP_OK) goto fail;
+        if ((rc = upload(&d.tcolor, P->thread_color.data(), P->thread_color.size(), bytes)) != MP_OK) goto fail;
+        {
+            std::vector<int32_t> all;
+            for (int s = 0; s < P->ntosets; ++s) all.insert(all.end(), P->fp_ids[s].begin(), P->fp_ids[s].end());
+            if ((rc = upload(&d.fp, all.data(), all.size(), bytes)) != MP_OK) goto fail;
+        }
+    } else {
+        for (int m = 0; m < P->nmaps; ++m)
+            if ((rc = upload(&d.map[m], P->maps[m].idx.data(), P->maps[m].idx.size(), bytes)) != MP_OK) goto fail;
+    }
+    d.device = dev;
+    d.bytes = bytes;
+    return MP_OK;
+fail:
+    d.device = dev;
+    mp_plan_free_device(P);
+    return rc;
+}
+
+extern "C" int mesh_plan_upload(mp_plan *plan)
+{
+    if (!plan) return MP_EINVAL;
+    return mp_plan_ensure_device(plan);
+}
+
+// ------------------------------------------------------------- scratch
+
+namespace {
+constexpr int kReduceParts = 152 * 4;  // one partial per CTA of the update grid
+std::mutex g_scratch_mu;
+double *g_partials[64] = {nullptr};
+__device__ int g_device_error;  // error word of bounded device-side waits
+}  // namespace
+
+int mp_reduce_scratch(double **partials, int *nparts)
+{
+    int dev = 0;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return MP_EINVAL;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_partials[dev]) MP_CUDA_TRY(cudaMalloc(&g_partials[dev], kReduceParts * sizeof(double)));
+    *partials = g_partials[dev];
+    *nparts = kReduceParts;
+    return MP_OK;
+}
+
+extern "C" int mp_check_device_status(void *stream)
+{
+    int h = 0;
+    MP_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_device_error, sizeof(int), 0, cudaMemcpyDeviceToHost,
+                                          as_stream(stream)));
+    MP_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    if (h) {
+        int zero = 0;
+        MP_CUDA_TRY(cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)));
+        return MP_ETIMEOUT;
+    }
+    return MP_OK;
+}
+
+// ------------------------------------------------------------ direct loops
+
+namespace {
+
+template <typename T>
+__global__ void save_soln_kernel(const T *__restrict__ q, T *__restrict__ qold, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        qold[i] = q[i];
+}
+
+// update (Airfoil's direct cell loop): d = res/adt in FP64, q = qold - d,
+// res = 0, and a fixed-order sum of d^2: thread-strided partial sums, a
+// fixed tree per CTA, one partial per CTA in scratch.
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(256) update_kernel(const T *__restrict__ qold, T *__restrict__ q,
+                                                     T *__restrict__ res, const T *__restrict__ adt,
+                                                     int64_t ncell, double *__restrict__ partials)
+{
+    double s = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        double ai = 1.0 / (double)adt[c];
+        for (int k = 0; k < 4; ++k) {
+            int64_t j = SOA ? k * ncell + c : 4 * c + k;
+            double d = (double)res[j] * ai;
+            q[j] = (T)((double)qold[j] - d);
+            res[j] = T(0);
+            s += d * d;
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double *__restrict__ partials, int n,
+                                                          double *__restrict__ out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s += partials[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out += red[0];
+}
+
+}  // namespace
+
+extern "C" int loop_save_soln(int64_t ncell, int32_t dtype, int32_t layout, const void *q, void *qold, void *stream)
+{
+    (void)layout;  // a plain copy of all 4*ncell values, layout-independent
+    if (ncell < 0 || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
+    if (ncell == 0) return MP_OK;
+    if (!q || !qold) return MP_EINVAL;
+    int64_t n = 4 * ncell;
+    int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    if (dtype == MP_F64)
+        save_soln_kernel<double><<<grid, 256, 0, as_stream(stream)>>>((const double *)q, (double *)qold, n);
+    else
+        save_soln_kernel<float><<<grid, 256, 0, as_stream(stream)>>>((const float *)q, (float *)qold, n);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+extern "C" int loop_update(int64_t ncell, int32_t dtype, int32_t layout, const void *qold, void *q, void *res,
+                           const void *adt, double *rms_dev, void *stream)
+{
+    if (ncell < 0 || (dtype != MP_F64 && dtype != MP_F32) || (layout != MP_LAYOUT_AOS && layout != MP_LAYOUT_SOA))
+        return MP_EINVAL;
+    if (ncell == 0) return MP_OK;
+    if (!qold || !q || !res || !adt || !rms_dev) return MP_EINVAL;
+    double *parts = nullptr;
+    int nparts = 0;
+    int rc = mp_reduce_scratch(&parts, &nparts);
+    if (rc != MP_OK) return rc;
+    cudaStream_t s = as_stream(stream);
+    bool soa = layout == MP_LAYOUT_SOA;
+    if (dtype == MP_F64) {
+        auto k = soa ? update_kernel<double, true> : update_kernel<double, false>;
+        k<<<nparts, 256, 0, s>>>((const double *)qold, (double *)q, (double *)res, (const double *)adt, ncell, parts);
+    } else {
+        auto k = soa ? update_kernel<float, true> : update_kernel<float, false>;
+        k<<<nparts, 256, 0, s>>>((const float *)qold, (float *)q, (float *)res, (const float *)adt, ncell, parts);
+    }
+    sum_partials_kernel<<<1, 256, 0, s>>>(parts, nparts, rms_dev);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}

@@ -1,0 +1,296 @@
+// Hex assembly (the access pattern of IntegrateStressForElems, Sec. 3.1.4):
+// per hex8 element gather x and v on 8 nodes, read sig directly, compute the
+// one-point stress force and Flanagan-Belytschko hourglass force, write the
+// element volume directly and increment the nodal force on 8 nodes.
+//
+// Variants (plan colouring): HIER stages the block's node footprint (x, v)
+// in shared memory and applies the 24 increments per element one thread
+// colour at a time, then writes each footprint node back once; GLOBAL runs
+// one launch per element colour with direct global read-add-writes; ATOMIC
+// uses atomicAdd on f.
+#include "common.cuh"
+
+namespace {
+
+// Corner signs of the reference element in the elem->node order:
+// (-,-,-),(+,-,-),(+,+,-),(-,+,-),(-,-,+),(+,-,+),(+,+,+),(-,+,+).
+__device__ __forceinline__ constexpr int sx(int i) { return (i == 1 || i == 2 || i == 5 || i == 6) ? 1 : -1; }
+__device__ __forceinline__ constexpr int sy(int i) { return (i == 2 || i == 3 || i == 6 || i == 7) ? 1 : -1; }
+__device__ __forceinline__ constexpr int sz(int i) { return i >= 4 ? 1 : -1; }
+
+// Element forces fe[i][a] (i = corner, a = component) and volume for corner
+// coordinates xe and velocities ve:
+//   J = 1/8 sum_i x_i xi_i^T, V = 8 det J, B_i = cof(J) xi_i,
+//   f_i = -diag(sig) B_i - kappa sum_k g_{k,i} sum_j g_{k,j} v_j,
+//   g_{k,i} = Gamma_{k,i} - (sum_j Gamma_{k,j} x_j) . B_i / V.
+template <typename T>
+__device__ __forceinline__ void hex_element(const T xe[8][3], const T ve[8][3], T s0, T s1, T s2, T kappa,
+                                            T fe[8][3], T &vol)
+{
+    T J[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T j0 = T(0), j1 = T(0), j2 = T(0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            j0 += sx(i) > 0 ? xe[i][a] : -xe[i][a];
+            j1 += sy(i) > 0 ? xe[i][a] : -xe[i][a];
+            j2 += sz(i) > 0 ? xe[i][a] : -xe[i][a];
+        }
+        J[a][0] = T(0.125) * j0;
+        J[a][1] = T(0.125) * j1;
+        J[a][2] = T(0.125) * j2;
+    }
+    T C[3][3];
+    C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    T det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    T V = T(8) * det;
+    vol = V;
+    T B[8][3];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            B[i][a] = (sx(i) > 0 ? C[a][0] : -C[a][0]) + (sy(i) > 0 ? C[a][1] : -C[a][1]) +
+                      (sz(i) > 0 ? C[a][2] : -C[a][2]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        fe[i][0] = -s0 * B[i][0];
+        fe[i][1] = -s1 * B[i][1];
+        fe[i][2] = -s2 * B[i][2];
+    }
+    const T iV = T(1) / V;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        // Gamma_k: eta zeta, xi zeta, xi eta, xi eta zeta
+        T h[3] = {T(0), T(0), T(0)};
+        int G[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            G[j] = k == 0 ? sy(j) * sz(j) : (k == 1 ? sx(j) * sz(j) : (k == 2 ? sx(j) * sy(j) : sx(j) * sy(j) * sz(j)));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) h[a] += G[j] > 0 ? xe[j][a] : -xe[j][a];
+        }
+        T g[8];
+        T qk[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            g[i] = T(G[i]) - (h[0] * B[i][0] + h[1] * B[i][1] + h[2] * B[i][2]) * iV;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) qk[a] += g[i] * ve[i][a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) qk[a] *= kappa;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) fe[i][a] -= g[i] * qk[a];
+    }
+}
+
+template <typename T, bool SOA>
+__device__ __forceinline__ void load3(const T *__restrict__ p, int64_t n, int64_t i, T &a, T &b, T &c)
+{
+    if (SOA) {
+        a = p[i];
+        b = p[n + i];
+        c = p[2 * n + i];
+    } else {
+        a = p[3 * i];
+        b = p[3 * i + 1];
+        c = p[3 * i + 2];
+    }
+}
+
+// smem per footprint node: x[3], v[3], f increments[3] and the global id
+template <typename T>
+__host__ __device__ constexpr int hex_smem_per_node()
+{
+    return 9 * (int)sizeof(T) + 4;
+}
+
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict__ desc, int block0,
+                                                const uint4 *__restrict__ lmap, const uint8_t *__restrict__ tcolor,
+                                                const int32_t *__restrict__ fp, const T *__restrict__ x,
+                                                const T *__restrict__ v, const T *__restrict__ sig,
+                                                T *__restrict__ f, T *__restrict__ vol, int64_t nnode,
+                                                int64_t nelem, int cap, T kappa)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_x = reinterpret_cast<T *>(smem_raw);  // [3][cap]
+    T *s_v = s_x + 3 * cap;                    // [3][cap]
+    T *s_f = s_v + 3 * cap;                    // [3][cap]
+    int *s_gid = reinterpret_cast<int *>(s_f + 3 * cap);
+
+    const mp_block_desc d = desc[block0 + blockIdx.x];
+    const int tid = threadIdx.x;
+    const int nn = d.fp_count[0];
+    const int32_t *fpn = fp + d.fp_start[0];
+    for (int i = tid; i < nn; i += blockDim.x) {
+        int g = fpn[i];
+        T a, b, c;
+        load3<T, SOA>(x, nnode, g, a, b, c);
+        s_x[i] = a;
+        s_x[cap + i] = b;
+        s_x[2 * cap + i] = c;
+        load3<T, SOA>(v, nnode, g, a, b, c);
+        s_v[i] = a;
+        s_v[cap + i] = b;
+        s_v[2 * cap + i] = c;
+        s_f[i] = T(0);
+        s_f[cap + i] = T(0);
+        s_f[2 * cap + i] = T(0);
+        s_gid[i] = g;
+    }
+    __syncthreads();
+    const bool active = tid < d.nitems;
+    T fe[8][3];
+    int loc[8];
+    int my_color = -1;
+    if (active) {
+        const int e = d.item_start + tid;
+        const uint4 l = lmap[e];
+        loc[0] = l.x & 0xffff;
+        loc[1] = l.x >> 16;
+        loc[2] = l.y & 0xffff;
+        loc[3] = l.y >> 16;
+        loc[4] = l.z & 0xffff;
+        loc[5] = l.z >> 16;
+        loc[6] = l.w & 0xffff;
+        loc[7] = l.w >> 16;
+        my_color = tcolor[e];
+        T xe[8][3], ve[8][3];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xe[i][a] = s_x[a * cap + loc[i]];
+                ve[i][a] = s_v[a * cap + loc[i]];
+            }
+        T s0, s1, s2, V;
+        load3<T, SOA>(sig, nelem, e, s0, s1, s2);
+        hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
+        vol[e] = V;
+    }
+    for (int c = 0; c < d.ncolors; ++c) {
+        if (my_color == c) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) s_f[a * cap + loc[i]] += fe[i][a];
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < nn; i += blockDim.x) {
+        int64_t g = s_gid[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int64_t j = SOA ? a * nnode + g : 3 * g + a;
+            f[j] += s_f[a * cap + i];
+        }
+    }
+}
+
+template <typename T, bool SOA, bool ATOMIC>
+__global__ void __launch_bounds__(256) hex_direct(int e0, int e1, const int32_t *__restrict__ e2n,
+                                                  const T *__restrict__ x, const T *__restrict__ v,
+                                                  const T *__restrict__ sig, T *__restrict__ f, T *__restrict__ vol,
+                                                  int64_t nnode, int64_t nelem, T kappa)
+{
+    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    int nd[8];
+    const int4 *row = reinterpret_cast<const int4 *>(e2n) + 2 * (int64_t)e;
+    int4 r0 = row[0], r1 = row[1];
+    nd[0] = r0.x;
+    nd[1] = r0.y;
+    nd[2] = r0.z;
+    nd[3] = r0.w;
+    nd[4] = r1.x;
+    nd[5] = r1.y;
+    nd[6] = r1.z;
+    nd[7] = r1.w;
+    T xe[8][3], ve[8][3], fe[8][3];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        load3<T, SOA>(x, nnode, nd[i], xe[i][0], xe[i][1], xe[i][2]);
+        load3<T, SOA>(v, nnode, nd[i], ve[i][0], ve[i][1], ve[i][2]);
+    }
+    T s0, s1, s2, V;
+    load3<T, SOA>(sig, nelem, e, s0, s1, s2);
+    hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
+    vol[e] = V;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int64_t j = SOA ? a * nnode + nd[i] : 3 * (int64_t)nd[i] + a;
+            if (ATOMIC)
+                atomicAdd(f + j, fe[i][a]);
+            else
+                f[j] += fe[i][a];
+        }
+}
+
+template <typename T, bool SOA>
+int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol,
+                    double kappa, cudaStream_t s)
+{
+    const int64_t nnode = P->maps[0].to_size, nelem = P->from_size;
+    if (P->opts.coloring == MP_COLOR_HIER) {
+        const int cap = P->stats.footprint_max[0];
+        const int smem = cap * hex_smem_per_node<T>();
+        auto kern = hex_hier<T, SOA>;
+        int rc = mp_allow_smem(kern, smem);
+        if (rc != MP_OK) return rc;
+        if (P->opts.block_size > 512) return MP_EINVAL;
+        for (int c = 0; c < P->ncolors; ++c) {
+            int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
+            if (nb == 0) continue;
+            kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const uint4 *>(P->dev.lmap),
+                                                      P->dev.tcolor, P->dev.fp, (const T *)x, (const T *)v,
+                                                      (const T *)sig, (T *)f, (T *)vol, nnode, nelem, cap, (T)kappa);
+        }
+    } else {
+        const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;
+        for (int c = 0; c < P->ncolors; ++c) {
+            int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
+            if (e1 <= e0) continue;
+            auto kern = atomic ? hex_direct<T, SOA, true> : hex_direct<T, SOA, false>;
+            kern<<<(e1 - e0 + 255) / 256, 256, 0, s>>>(e0, e1, P->dev.map[0], (const T *)x, (const T *)v,
+                                                       (const T *)sig, (T *)f, (T *)vol, nnode, nelem, (T)kappa);
+        }
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" int loop_elem_assemble(const mp_plan *P, int32_t dtype, const void *x, const void *v, const void *sig,
+                                  void *f, void *vol, double kappa, void *stream)
+{
+    if (!P || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
+    if (P->nmaps != 1 || P->maps[0].arity != 8 || !P->maps[0].written) return MP_EPLAN;
+    if (P->from_size == 0) return MP_OK;
+    for (const void *p : {x, v, sig, (const void *)f, (const void *)vol})
+        if (!p || !aligned16(p)) return MP_EINVAL;
+    int rc = mp_plan_ensure_device(P);
+    if (rc != MP_OK) return rc;
+    cudaStream_t s = as_stream(stream);
+    bool soa = P->opts.layout == MP_LAYOUT_SOA;
+    if (dtype == MP_F64)
+        return soa ? elem_assemble_t<double, true>(P, x, v, sig, f, vol, kappa, s)
+                   : elem_assemble_t<double, false>(P, x, v, sig, f, vol, kappa, s);
+    return soa ? elem_assemble_t<float, true>(P, x, v, sig, f, vol, kappa, s)
+               : elem_assemble_t<float, false>(P, x, v, sig, f, vol, kappa, s);
+}

@@ -1,0 +1,489 @@
+// Airfoil-style edge loops: res_calc (three race-avoidance strategies),
+// bres_calc and adt_calc.
+//
+// res_calc strategies (Sec. 2.1 and 2.2 of the paper):
+//   HIER   staged two-layer colouring (Algorithm 1): one CTA per block of a
+//          block colour; the block's cell and node footprint is gathered into
+//          shared memory with coalesced (vector) loads and per-cell
+//          primitives are computed once per staged cell; each thread computes
+//          one edge flux from shared memory; increments are applied to shared
+//          memory one thread colour at a time; every footprint cell is
+//          written back once with a plain read-add-write (no atomics: blocks
+//          of one colour share no cell).
+//   GLOBAL one launch per edge colour; every thread gathers its two cells and
+//          two nodes from global memory and read-add-writes res directly.
+//   ATOMIC one launch; increments with FP64/FP32 atomicAdd.
+#include "common.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ HIER
+
+// Dynamic shared memory layout for a block with cap_c cells and cap_n nodes:
+//   T  q[4][cap_c], adt[cap_c], u[cap_c], v[cap_c], p[cap_c], H[cap_c]
+//   T  inc[4][cap_c]
+//   T  xh[2][cap_n]          (half coordinates, n/2 = differences of these)
+//   int gid[cap_c]
+template <typename T>
+__host__ __device__ constexpr int res_smem_per_cell()
+{
+    return 13 * (int)sizeof(T) + 4;
+}
+template <typename T>
+__host__ __device__ constexpr int res_smem_per_node()
+{
+    return 2 * (int)sizeof(T);
+}
+
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__restrict__ desc, int block0,
+                                                      const ushort4 *__restrict__ lmap,
+                                                      const uint8_t *__restrict__ tcolor,
+                                                      const int32_t *__restrict__ fp, const T *__restrict__ x,
+                                                      const T *__restrict__ q, const T *__restrict__ adt,
+                                                      T *__restrict__ res, int64_t nnode, int64_t ncell, int cap_c,
+                                                      int cap_n, T gm1, T half_eps)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_q = reinterpret_cast<T *>(smem_raw);
+    T *s_adt = s_q + 4 * cap_c;
+    T *s_u = s_adt + cap_c;
+    T *s_v = s_u + cap_c;
+    T *s_p = s_v + cap_c;
+    T *s_H = s_p + cap_c;
+    T *s_inc = s_H + cap_c;
+    T *s_xh = s_inc + 4 * cap_c;
+    int *s_gid = reinterpret_cast<int *>(s_xh + 2 * cap_n);
+
+    const mp_block_desc d = desc[block0 + blockIdx.x];
+    const int tid = threadIdx.x;
+    const int nn = d.fp_count[0], nc = d.fp_count[1];
+    const int32_t *fpn = fp + d.fp_start[0];
+    const int32_t *fpc = fp + d.fp_start[1];
+
+    // stage cells: q, adt and per-cell primitives; zero the increments
+    for (int i = tid; i < nc; i += blockDim.x) {
+        int g = fpc[i];
+        T r, ru, rv, E;
+        if (SOA) {
+            r = q[g];
+            ru = q[ncell + g];
+            rv = q[2 * ncell + g];
+            E = q[3 * ncell + g];
+        } else if (sizeof(T) == 8) {
+            const double2 *q2 = reinterpret_cast<const double2 *>(q) + 2 * (int64_t)g;
+            double2 a = q2[0], b = q2[1];
+            r = (T)a.x;
+            ru = (T)a.y;
+            rv = (T)b.x;
+            E = (T)b.y;
+        } else {
+            float4 a = reinterpret_cast<const float4 *>(q)[g];
+            r = (T)a.x;
+            ru = (T)a.y;
+            rv = (T)a.z;
+            E = (T)a.w;
+        }
+        T u, v, p, H;
+        cell_prims(r, ru, rv, E, gm1, u, v, p, H);
+        s_q[i] = r;
+        s_q[cap_c + i] = ru;
+        s_q[2 * cap_c + i] = rv;
+        s_q[3 * cap_c + i] = E;
+        s_adt[i] = adt[g];
+        s_u[i] = u;
+        s_v[i] = v;
+        s_p[i] = p;
+        s_H[i] = H;
+        s_inc[i] = T(0);
+        s_inc[cap_c + i] = T(0);
+        s_inc[2 * cap_c + i] = T(0);
+        s_inc[3 * cap_c + i] = T(0);
+        s_gid[i] = g;
+    }
+    // stage nodes as half coordinates (exact scaling by 1/2)
+    for (int i = tid; i < nn; i += blockDim.x) {
+        int g = fpn[i];
+        T px, py;
+        if (SOA) {
+            px = x[g];
+            py = x[nnode + g];
+        } else if (sizeof(T) == 8) {
+            double2 a = reinterpret_cast<const double2 *>(x)[g];
+            px = (T)a.x;
+            py = (T)a.y;
+        } else {
+            float2 a = reinterpret_cast<const float2 *>(x)[g];
+            px = (T)a.x;
+            py = (T)a.y;
+        }
+        s_xh[i] = T(0.5) * px;
+        s_xh[cap_n + i] = T(0.5) * py;
+    }
+    __syncthreads();
+
+    const bool active = tid < d.nitems;
+    T f[4] = {T(0), T(0), T(0), T(0)};
+    int c1 = 0, c2 = 0, my_color = -1;
+    if (active) {
+        const int it = d.item_start + tid;
+        const ushort4 l = lmap[it];
+        my_color = tcolor[it];
+        const int na = l.x, nb = l.y;
+        c1 = l.z;
+        c2 = l.w;
+        T nxh = s_xh[cap_n + na] - s_xh[cap_n + nb];
+        T nyh = s_xh[nb] - s_xh[na];
+        edge_flux(nxh, nyh, s_q[c1], s_q[cap_c + c1], s_q[2 * cap_c + c1], s_q[3 * cap_c + c1], s_u[c1], s_v[c1],
+                  s_p[c1], s_H[c1], s_adt[c1], s_q[c2], s_q[cap_c + c2], s_q[2 * cap_c + c2], s_q[3 * cap_c + c2],
+                  s_u[c2], s_v[c2], s_p[c2], s_H[c2], s_adt[c2], half_eps, f);
+    }
+    // thread-coloured increments in shared memory (Algorithm 1)
+    for (int c = 0; c < d.ncolors; ++c) {
+        if (my_color == c) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                s_inc[k * cap_c + c1] += f[k];
+                s_inc[k * cap_c + c2] -= f[k];
+            }
+        }
+        __syncthreads();
+    }
+    // one coalesced read-add-write per footprint cell
+    for (int i = tid; i < nc; i += blockDim.x) {
+        int g = s_gid[i];
+        if (SOA) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) res[k * ncell + g] += s_inc[k * cap_c + i];
+        } else if (sizeof(T) == 8) {
+            double2 *r2 = reinterpret_cast<double2 *>(res) + 2 * (int64_t)g;
+            double2 a = r2[0], b = r2[1];
+            a.x += (double)s_inc[i];
+            a.y += (double)s_inc[cap_c + i];
+            b.x += (double)s_inc[2 * cap_c + i];
+            b.y += (double)s_inc[3 * cap_c + i];
+            r2[0] = a;
+            r2[1] = b;
+        } else {
+            float4 *r4 = reinterpret_cast<float4 *>(res) + g;
+            float4 a = *r4;
+            a.x += (float)s_inc[i];
+            a.y += (float)s_inc[cap_c + i];
+            a.z += (float)s_inc[2 * cap_c + i];
+            a.w += (float)s_inc[3 * cap_c + i];
+            *r4 = a;
+        }
+    }
+}
+
+// ------------------------------------------------------- GLOBAL / ATOMIC
+
+template <typename T, bool SOA>
+__device__ __forceinline__ void load_cell(const T *__restrict__ q, int64_t ncell, int g, T &r, T &ru, T &rv, T &E)
+{
+    if (SOA) {
+        r = q[g];
+        ru = q[ncell + g];
+        rv = q[2 * ncell + g];
+        E = q[3 * ncell + g];
+    } else if (sizeof(T) == 8) {
+        const double2 *q2 = reinterpret_cast<const double2 *>(q) + 2 * (int64_t)g;
+        double2 a = q2[0], b = q2[1];
+        r = (T)a.x;
+        ru = (T)a.y;
+        rv = (T)b.x;
+        E = (T)b.y;
+    } else {
+        float4 a = reinterpret_cast<const float4 *>(q)[g];
+        r = (T)a.x;
+        ru = (T)a.y;
+        rv = (T)a.z;
+        E = (T)a.w;
+    }
+}
+
+template <typename T, bool SOA>
+__device__ __forceinline__ void load_node(const T *__restrict__ x, int64_t nnode, int g, T &px, T &py)
+{
+    if (SOA) {
+        px = x[g];
+        py = x[nnode + g];
+    } else if (sizeof(T) == 8) {
+        double2 a = reinterpret_cast<const double2 *>(x)[g];
+        px = (T)a.x;
+        py = (T)a.y;
+    } else {
+        float2 a = reinterpret_cast<const float2 *>(x)[g];
+        px = (T)a.x;
+        py = (T)a.y;
+    }
+}
+
+// One thread per edge of [e0, e1): gather from global, flux, then either a
+// plain read-add-write (edges of one colour share no cell) or atomics.
+template <typename T, bool SOA, bool ATOMIC>
+__global__ void __launch_bounds__(256) res_calc_direct(int e0, int e1, const int32_t *__restrict__ e2n,
+                                                       const int32_t *__restrict__ e2c, const T *__restrict__ x,
+                                                       const T *__restrict__ q, const T *__restrict__ adt,
+                                                       T *__restrict__ res, int64_t nnode, int64_t ncell, T gm1,
+                                                       T half_eps)
+{
+    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    int2 nab = reinterpret_cast<const int2 *>(e2n)[e];
+    int2 cc = reinterpret_cast<const int2 *>(e2c)[e];
+    T xa, ya, xb, yb;
+    load_node<T, SOA>(x, nnode, nab.x, xa, ya);
+    load_node<T, SOA>(x, nnode, nab.y, xb, yb);
+    T r1, ru1, rv1, E1, r2, ru2, rv2, E2;
+    load_cell<T, SOA>(q, ncell, cc.x, r1, ru1, rv1, E1);
+    load_cell<T, SOA>(q, ncell, cc.y, r2, ru2, rv2, E2);
+    T a1 = adt[cc.x], a2 = adt[cc.y];
+    T u1, v1, p1, H1, u2, v2, p2, H2;
+    cell_prims(r1, ru1, rv1, E1, gm1, u1, v1, p1, H1);
+    cell_prims(r2, ru2, rv2, E2, gm1, u2, v2, p2, H2);
+    T nxh = T(0.5) * ya - T(0.5) * yb;
+    T nyh = T(0.5) * xb - T(0.5) * xa;
+    T f[4];
+    edge_flux(nxh, nyh, r1, ru1, rv1, E1, u1, v1, p1, H1, a1, r2, ru2, rv2, E2, u2, v2, p2, H2, a2, half_eps, f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int64_t j1 = SOA ? k * ncell + cc.x : 4 * (int64_t)cc.x + k;
+        int64_t j2 = SOA ? k * ncell + cc.y : 4 * (int64_t)cc.y + k;
+        if (ATOMIC) {
+            atomicAdd(res + j1, f[k]);
+            atomicAdd(res + j2, -f[k]);
+        } else {
+            res[j1] += f[k];
+            res[j2] -= f[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------- bres_calc
+
+// Far-field boundary edges: q_b = (q_c + qinf)/2,
+// res[c] += F(q_b).n + eps adt_c (q_c - qinf).
+template <typename T, bool SOA, bool ATOMIC>
+__global__ void __launch_bounds__(256) bres_calc_direct(int e0, int e1, const int32_t *__restrict__ b2n,
+                                                        const int32_t *__restrict__ b2c, const T *__restrict__ x,
+                                                        const T *__restrict__ q, const T *__restrict__ adt,
+                                                        T *__restrict__ res, int64_t nnode, int64_t ncell, T gm1,
+                                                        T eps, T qi0, T qi1, T qi2, T qi3)
+{
+    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    int2 nab = reinterpret_cast<const int2 *>(b2n)[e];
+    int c = b2c[e];
+    T xa, ya, xb, yb;
+    load_node<T, SOA>(x, nnode, nab.x, xa, ya);
+    load_node<T, SOA>(x, nnode, nab.y, xb, yb);
+    T qc[4];
+    load_cell<T, SOA>(q, ncell, c, qc[0], qc[1], qc[2], qc[3]);
+    const T qi[4] = {qi0, qi1, qi2, qi3};
+    T qb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qb[k] = T(0.5) * (qc[k] + qi[k]);
+    T u, v, p, H;
+    cell_prims(qb[0], qb[1], qb[2], qb[3], gm1, u, v, p, H);
+    T nx = ya - yb, ny = xb - xa;
+    T V = u * nx + v * ny;
+    T ea = eps * adt[c];
+    T f[4];
+    f[0] = qb[0] * V + ea * (qc[0] - qi[0]);
+    f[1] = qb[1] * V + p * nx + ea * (qc[1] - qi[1]);
+    f[2] = qb[2] * V + p * ny + ea * (qc[2] - qi[2]);
+    f[3] = H * V + ea * (qc[3] - qi[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int64_t j = SOA ? k * ncell + c : 4 * (int64_t)c + k;
+        if (ATOMIC)
+            atomicAdd(res + j, f[k]);
+        else
+            res[j] += f[k];
+    }
+}
+
+// ------------------------------------------------------------- adt_calc
+
+// Cell loop with read-only indirection: adt = sum over the 4 sides of
+// (|u dy - v dx| + c sqrt(dx^2 + dy^2)) / cfl,  c = sqrt(gam p / rho).
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(256) adt_calc_kernel(int64_t n, const int32_t *__restrict__ c2n,
+                                                       const T *__restrict__ x, const T *__restrict__ q,
+                                                       T *__restrict__ adt, int64_t nnode, T gam, T gm1,
+                                                       T inv_cfl)
+{
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int4 nd = reinterpret_cast<const int4 *>(c2n)[c];
+    T r, ru, rv, E;
+    load_cell<T, SOA>(q, n, (int)c, r, ru, rv, E);
+    T ri = T(1) / r;
+    T u = ru * ri, v = rv * ri;
+    T p = gm1 * (E - T(0.5) * (ru * u + rv * v));
+    T cs = sqrt(gam * p * ri);
+    T px[4], py[4];
+    load_node<T, SOA>(x, nnode, nd.x, px[0], py[0]);
+    load_node<T, SOA>(x, nnode, nd.y, px[1], py[1]);
+    load_node<T, SOA>(x, nnode, nd.z, px[2], py[2]);
+    load_node<T, SOA>(x, nnode, nd.w, px[3], py[3]);
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        T dx = px[(k + 1) & 3] - px[k];
+        T dy = py[(k + 1) & 3] - py[k];
+        s += fabs(u * dy - v * dx) + cs * sqrt(dx * dx + dy * dy);
+    }
+    adt[c] = s * inv_cfl;
+}
+
+// --------------------------------------------------------------- drivers
+
+bool check_maps(const mp_plan *P, int a0, int w0, int a1, int w1)
+{
+    return P->nmaps == 2 && P->maps[0].arity == a0 && P->maps[1].arity == a1 && P->maps[0].written == w0 &&
+           P->maps[1].written == w1;
+}
+
+template <typename T, bool SOA>
+int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, void *res, double gam, double eps,
+               cudaStream_t s)
+{
+    const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
+    const T gm1 = (T)(gam - 1.0), half_eps = (T)(0.5 * eps);
+    const int co = P->opts.coloring;
+    if (co == MP_COLOR_HIER) {
+        if (P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
+        const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
+        const int smem = cap_c * res_smem_per_cell<T>() + cap_n * res_smem_per_node<T>();
+        auto kern = res_calc_hier<T, SOA>;
+        int rc = mp_allow_smem(kern, smem);
+        if (rc != MP_OK) return rc;
+        const int32_t *fp = P->dev.fp;
+        for (int c = 0; c < P->ncolors; ++c) {
+            int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
+            if (nb == 0) continue;
+            kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
+                                                      P->dev.tcolor, fp, (const T *)x, (const T *)q, (const T *)adt,
+                                                      (T *)res, nnode, ncell, cap_c, cap_n, gm1, half_eps);
+        }
+    } else {
+        const bool atomic = co == MP_COLOR_ATOMIC;
+        for (int c = 0; c < P->ncolors; ++c) {
+            int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
+            if (e1 <= e0) continue;
+            int grid = (e1 - e0 + 255) / 256;
+            auto kern = atomic ? res_calc_direct<T, SOA, true> : res_calc_direct<T, SOA, false>;
+            kern<<<grid, 256, 0, s>>>(e0, e1, P->dev.map[0], P->dev.map[1], (const T *)x, (const T *)q, (const T *)adt,
+                                      (T *)res, nnode, ncell, gm1, half_eps);
+        }
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+template <typename T, bool SOA>
+int bres_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, void *res, const double *qinf,
+                double gam, double eps, cudaStream_t s)
+{
+    const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
+    const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;
+    // HIER plans of this loop run their block colours as global colours
+    // would: each block colour's iterations share no cell.
+    for (int c = 0; c < P->ncolors; ++c) {
+        int e0, e1;
+        if (P->opts.coloring == MP_COLOR_HIER) {
+            e0 = P->block_offsets[P->color_offsets[c]];
+            e1 = P->block_offsets[P->color_offsets[c + 1]];
+        } else {
+            e0 = P->color_offsets[c];
+            e1 = P->color_offsets[c + 1];
+        }
+        if (e1 <= e0) continue;
+        int grid = (e1 - e0 + 255) / 256;
+        auto kern = atomic ? bres_calc_direct<T, SOA, true> : bres_calc_direct<T, SOA, false>;
+        kern<<<grid, 256, 0, s>>>(e0, e1, P->dev.map[0], P->dev.map[1], (const T *)x, (const T *)q, (const T *)adt,
+                                  (T *)res, nnode, ncell, (T)(gam - 1.0), (T)eps, (T)qinf[0], (T)qinf[1], (T)qinf[2],
+                                  (T)qinf[3]);
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+bool data_ok(std::initializer_list<const void *> ptrs)
+{
+    for (const void *p : ptrs)
+        if (!p || !aligned16(p)) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" int loop_res_calc(const mp_plan *P, int32_t dtype, const void *x, const void *q, const void *adt,
+                             void *res, double gam, double eps, void *stream)
+{
+    if (!P || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
+    // edge->node may be marked written: an adjoint plan (both maps coloured)
+    // also runs the forward loop in the same numbering
+    if (!check_maps(P, 2, 0, 2, 1) && !check_maps(P, 2, 1, 2, 1)) return MP_EPLAN;
+    if (P->from_size == 0) return MP_OK;
+    if (!data_ok({x, q, adt, res})) return MP_EINVAL;
+    int rc = mp_plan_ensure_device(P);
+    if (rc != MP_OK) return rc;
+    cudaStream_t s = as_stream(stream);
+    bool soa = P->opts.layout == MP_LAYOUT_SOA;
+    if (dtype == MP_F64)
+        return soa ? res_calc_t<double, true>(P, x, q, adt, res, gam, eps, s)
+                   : res_calc_t<double, false>(P, x, q, adt, res, gam, eps, s);
+    return soa ? res_calc_t<float, true>(P, x, q, adt, res, gam, eps, s)
+               : res_calc_t<float, false>(P, x, q, adt, res, gam, eps, s);
+}
+
+extern "C" int loop_bres_calc(const mp_plan *P, int32_t dtype, const void *x, const void *q, const void *adt,
+                              void *res, const double *qinf, double gam, double eps, void *stream)
+{
+    if (!P || !qinf || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
+    if (!check_maps(P, 2, 0, 1, 1)) return MP_EPLAN;
+    if (P->from_size == 0) return MP_OK;
+    if (!data_ok({x, q, adt, res})) return MP_EINVAL;
+    // the direct kernels read the global maps: GLOBAL or ATOMIC plans, or
+    // HIER plans (which keep no global maps) are rejected here
+    if (P->opts.coloring == MP_COLOR_HIER) return MP_EPLAN;
+    int rc = mp_plan_ensure_device(P);
+    if (rc != MP_OK) return rc;
+    cudaStream_t s = as_stream(stream);
+    bool soa = P->opts.layout == MP_LAYOUT_SOA;
+    if (dtype == MP_F64)
+        return soa ? bres_calc_t<double, true>(P, x, q, adt, res, qinf, gam, eps, s)
+                   : bres_calc_t<double, false>(P, x, q, adt, res, qinf, gam, eps, s);
+    return soa ? bres_calc_t<float, true>(P, x, q, adt, res, qinf, gam, eps, s)
+               : bres_calc_t<float, false>(P, x, q, adt, res, qinf, gam, eps, s);
+}
+
+extern "C" int loop_adt_calc(const mp_plan *P, int32_t dtype, const void *x, const void *q, void *adt, double gam,
+                             double cfl, void *stream)
+{
+    if (!P || (dtype != MP_F64 && dtype != MP_F32) || !(cfl > 0)) return MP_EINVAL;
+    if (P->nmaps != 1 || P->maps[0].arity != 4) return MP_EPLAN;
+    if (P->opts.coloring == MP_COLOR_HIER) return MP_EPLAN;
+    if (P->from_size == 0) return MP_OK;
+    if (!data_ok({x, q, adt})) return MP_EINVAL;
+    int rc = mp_plan_ensure_device(P);
+    if (rc != MP_OK) return rc;
+    cudaStream_t s = as_stream(stream);
+    bool soa = P->opts.layout == MP_LAYOUT_SOA;
+    int64_t n = P->from_size, nnode = P->maps[0].to_size;
+    int grid = (int)((n + 255) / 256);
+    if (dtype == MP_F64) {
+        auto k = soa ? adt_calc_kernel<double, true> : adt_calc_kernel<double, false>;
+        k<<<grid, 256, 0, s>>>(n, P->dev.map[0], (const double *)x, (const double *)q, (double *)adt, nnode, gam,
+                               gam - 1.0, 1.0 / cfl);
+    } else {
+        auto k = soa ? adt_calc_kernel<float, true> : adt_calc_kernel<float, false>;
+        k<<<grid, 256, 0, s>>>(n, P->dev.map[0], (const float *)x, (const float *)q, (float *)adt, nnode,
+                               (float)gam, (float)(gam - 1.0), (float)(1.0 / cfl));
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}

@@ -1,0 +1,182 @@
+"""Host planner (C++ through the C ABI) against the plain-Python plan oracle
+and the plan invariants.  CPU only: mesh_plan_build touches no GPU."""
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import plan as PO
+
+ml = pytest.importorskip("paper_1802_03749_gb300")
+
+
+@pytest.fixture(scope="module")
+def mesh():
+    return meshgen.quad_mesh(60, 30, seed=4)
+
+
+def res_maps(m, adjoint=False):
+    return [{"to_set": 1, "idx": m.edge2node, "to_size": m.nnode, "written": adjoint},
+            {"to_set": 2, "idx": m.edge2cell, "to_size": m.ncell, "written": True}]
+
+
+def oracle_maps(m, P, adjoint=False):
+    """Plan-numbered maps as dicts for the Python oracle."""
+    e2n = P.table("map", 0).reshape(-1, 2)
+    e2c = P.table("map", 1).reshape(-1, 2)
+    return [{"to_set": 1, "idx": e2n, "to_size": m.nnode, "written": adjoint},
+            {"to_set": 2, "idx": e2c, "to_size": m.ncell, "written": True}]
+
+
+def check_perm_consistency(m, P):
+    """Plan-numbered maps = original maps renumbered by the plan's perms."""
+    pe, pn, pc = P.perm(0), P.perm(1), P.perm(2)
+    assert PO.is_permutation(pe, m.nedge)
+    assert PO.is_permutation(pn, m.nnode)
+    assert PO.is_permutation(pc, m.ncell)
+    inv_n = np.empty_like(pn)
+    inv_n[pn] = np.arange(m.nnode)
+    inv_c = np.empty_like(pc)
+    inv_c[pc] = np.arange(m.ncell)
+    assert np.array_equal(P.table("map", 0).reshape(-1, 2), inv_n[m.edge2node[pe]])
+    assert np.array_equal(P.table("map", 1).reshape(-1, 2), inv_c[m.edge2cell[pe]])
+
+
+@pytest.mark.parametrize("reorder", ["none", "rcm", "partition"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_hier_plan_matches_oracle(mesh, reorder, adjoint):
+    m = mesh
+    P = ml.Plan(res_maps(m, adjoint), m.nedge, block_size=256, reorder=reorder, coloring="hier")
+    check_perm_consistency(m, P)
+    st = P.stats()
+    bo = P.table("block_offsets")
+    co = P.table("color_offsets")
+    bc = P.table("block_color")
+    tc = P.table("thread_color")
+    assert bo[0] == 0 and bo[-1] == m.nedge and np.all(np.diff(bo) >= 1)
+    sprime = int(256 / 1.001) if reorder == "partition" else 256
+    assert np.diff(bo).max() <= sprime and st["sprime"] == int(256 / 1.001)
+    maps = oracle_maps(m, P, adjoint)
+    wrows = PO.written_rows_of(maps)
+    blocks = [list(range(bo[b], bo[b + 1])) for b in range(len(bo) - 1)]
+    # block colours: bit-exact first fit in the plan's block order, and sorted
+    # by colour (the plan renumbers blocks colour-major after colouring, a
+    # stable sort of the first-fit order, so first fit on the sorted order
+    # gives the same colours)
+    assert list(bc) == PO.block_colors(blocks, wrows)
+    assert np.all(np.diff(bc) >= 0)
+    assert np.array_equal(co, np.searchsorted(bc, np.arange(bc.max() + 2)))
+    # thread colours: first fit within each block (items are colour-sorted,
+    # and a stable sort of first-fit colours reproduces itself)
+    for b in blocks:
+        assert [tc[i] for i in b] == PO.thread_colors(b, wrows)
+        assert all(tc[b[i]] <= tc[b[i + 1]] for i in range(len(b) - 1))
+    assert PO.check_coloring(wrows, list(tc), groups=blocks)
+    # block colouring invariant: same-colour blocks share no written point
+    owner = {}
+    for b, items in enumerate(blocks):
+        for i in items:
+            for p in wrows[i]:
+                k = (bc[b], p)
+                assert owner.get(k, b) == b
+                owner[k] = b
+    assert st["reuse_all"] == pytest.approx(PO.reuse_factor(bo, [maps[0]["idx"], maps[1]["idx"]]))
+
+
+@pytest.mark.parametrize("reorder", ["rcm", "partition"])
+def test_footprints_and_local_maps(mesh, reorder):
+    """What the staged kernels index: fp[start[b,slot] + local[it,k]] is the
+    plan-numbered point of map slot k of iteration it, and each block's
+    footprint is sorted and duplicate-free."""
+    m = mesh
+    P = ml.Plan(res_maps(m), m.nedge, block_size=480, reorder=reorder, coloring="hier")
+    bo = P.table("block_offsets")
+    fp = P.table("footprint")
+    fs = P.table("fp_start").reshape(-1, 2)
+    fc = P.table("fp_count").reshape(-1, 2)
+    lm = P.table("local_map").reshape(m.nedge, -1)
+    e2n = P.table("map", 0).reshape(-1, 2)
+    e2c = P.table("map", 1).reshape(-1, 2)
+    slot_of = [0, 0, 1, 1]
+    glob = np.concatenate([e2n, e2c], axis=1)
+    st = P.stats()
+    for b in range(len(bo) - 1):
+        for s in range(2):
+            lst = fp[fs[b, s]:fs[b, s] + fc[b, s]]
+            assert np.all(np.diff(lst) > 0)
+        for it in range(bo[b], bo[b + 1]):
+            for k in range(4):
+                s = slot_of[k]
+                assert lm[it, k] < fc[b, s]
+                assert fp[fs[b, s] + lm[it, k]] == glob[it, k]
+    assert fc[:, 0].max() == st["footprint_max"][0] and fc[:, 1].max() == st["footprint_max"][1]
+
+
+def test_rcm_matches_oracle(mesh):
+    m = mesh
+    P = ml.Plan(res_maps(m), m.nedge, block_size=256, reorder="rcm", coloring="atomic")
+    maps = [{"to_set": 1, "idx": m.edge2node, "to_size": m.nnode, "written": False},
+            {"to_set": 2, "idx": m.edge2cell, "to_size": m.ncell, "written": True}]
+    ref = PO.rcm_plan_perms(maps, m.nedge, primary=1)
+    assert np.array_equal(P.perm(2), ref[2])
+    assert np.array_equal(P.perm(0), ref[0])
+    assert np.array_equal(P.perm(1), ref[1])
+
+
+def test_global_coloring_matches_oracle(mesh):
+    m = mesh
+    P = ml.Plan(res_maps(m), m.nedge, block_size=256, reorder="rcm", coloring="global")
+    check_perm_consistency(m, P)
+    co = P.table("color_offsets")
+    tc = P.table("thread_color")
+    maps = oracle_maps(m, P)
+    wrows = PO.written_rows_of(maps)
+    # items are sorted by colour: first fit over the RCM order, stably sorted
+    Pr = ml.Plan(res_maps(m), m.nedge, block_size=256, reorder="rcm", coloring="atomic")
+    wr = PO.written_rows_of(oracle_maps(m, Pr))
+    col = PO.first_fit_items(wr)
+    assert sorted(col) == list(tc)
+    assert PO.check_coloring(wrows, list(tc))
+    assert np.array_equal(co, np.searchsorted(tc, np.arange(tc.max() + 2)))
+
+
+def test_partition_data_reorder_groups_points(mesh):
+    """After the data-point reorder, points are sorted by the key (number of
+    accessing blocks, accessing block ids)."""
+    m = mesh
+    P = ml.Plan(res_maps(m), m.nedge, block_size=256, reorder="partition", coloring="hier")
+    bo = P.table("block_offsets")
+    blk = np.repeat(np.arange(len(bo) - 1), np.diff(bo))
+    e2c = P.table("map", 1).reshape(-1, 2)
+    order = PO.data_point_order(blk, [e2c], m.ncell)
+    assert order == list(range(m.ncell))
+
+
+def test_errors():
+    idx = np.array([[0, 1], [1, 5]], dtype=np.int32)
+    with pytest.raises(ml.MeshLoopError) as e:
+        ml.Plan([{"to_set": 1, "idx": idx, "to_size": 3, "written": True}], 2)
+    assert e.value.name == "MP_EMAPRANGE"
+    with pytest.raises(ml.MeshLoopError) as e:
+        ml.Plan([{"to_set": 1, "idx": idx, "to_size": 6, "written": True}], 2, block_size=100)
+    assert e.value.name == "MP_EINVAL"
+    # a star: 300 iterations all writing point 0 need 300 colours > 256
+    star = np.stack([np.zeros(300, np.int32), np.arange(1, 301, dtype=np.int32)], axis=1)
+    with pytest.raises(ml.MeshLoopError) as e:
+        ml.Plan([{"to_set": 1, "idx": star, "to_size": 301, "written": True}], 300, reorder="none",
+                coloring="global")
+    assert e.value.name == "MP_ECOLORS"
+    # more than 64 thread colours inside one block
+    with pytest.raises(ml.MeshLoopError) as e:
+        ml.Plan([{"to_set": 1, "idx": star[:100], "to_size": 301, "written": True}], 100, reorder="none",
+                coloring="hier", block_size=128)
+    assert e.value.name == "MP_ECOLORS"
+
+
+def test_map_renumber_roundtrip():
+    m = meshgen.quad_mesh(10, 6, seed=1)
+    pc = meshgen.permutation(5, 1, m.ncell).astype(np.int32)
+    pn = meshgen.permutation(5, 2, m.nnode).astype(np.int32)
+    out = ml.mesh_map_renumber(m.cell2node, pc, pn, m.nnode)
+    inv = np.empty_like(pn)
+    inv[pn] = np.arange(m.nnode)
+    assert np.array_equal(out, inv[m.cell2node[pc]])
