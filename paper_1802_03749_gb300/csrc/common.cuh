@@ -29,6 +29,20 @@ struct dat {
     __device__ __forceinline__ T &at(int64_t i, int k) const { return SOA ? p[k * n + i] : p[i * DIM + k]; }
 };
 
+// Size of the dynamic shared memory this CTA was launched with.
+__device__ __forceinline__ unsigned dynamic_smem_bytes()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+// Device error word codes (read by mp_check_device_status).
+enum { MP_DEVERR_NONE = 0, MP_DEVERR_TIMEOUT = 1, MP_DEVERR_SMEM = 2 };
+
+// Library-owned device error word of the current device.
+int mp_device_error_word(int **word);
+
 // Uploads the plan's tables to the current device if not done yet.
 int mp_plan_ensure_device(const mp_plan *plan);
 

@@ -36,12 +36,12 @@ __device__ __forceinline__ void flux_rev(T r, T ru, T rv, T u, T v, T p, T H, T 
     nby += h[2] * p + Wb * rv;
 }
 
-// smem per cell: q[4], adt, u, v, p, H, ri, rb[4], inc[4] (17 T) + gid;
+// smem per cell: q[4], adt, u, v, p, H, ri, rb[4], inc[4] (18 T) + gid;
 // per node: x[2], inc[2] (4 T) + gid
 template <typename T>
 __host__ __device__ constexpr int adj_smem_per_cell()
 {
-    return 17 * (int)sizeof(T) + 4;
+    return 18 * (int)sizeof(T) + 4;
 }
 template <typename T>
 __host__ __device__ constexpr int adj_smem_per_node()
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
                                                      const T *__restrict__ q, const T *__restrict__ adt,
                                                      const T *__restrict__ rbar, T *__restrict__ qbar,
                                                      T *__restrict__ xbar, int64_t nnode, int64_t ncell, int cap_c,
-                                                     int cap_n, T gm1, T half_eps)
+                                                     int cap_n, T gm1, T half_eps, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_q = reinterpret_cast<T *>(smem_raw);  // [4][cap_c]
@@ -77,6 +77,11 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
+    if ((unsigned)(reinterpret_cast<unsigned char *>(s_gn + cap_n) - smem_raw) > dynamic_smem_bytes() ||
+        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x) {
+        if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
+        return;
+    }
     const int32_t *fpn = fp + d.fp_start[0];
     const int32_t *fpc = fp + d.fp_start[1];
     for (int i = tid; i < nc; i += blockDim.x) {
@@ -253,13 +258,15 @@ int adjoint_t(const mp_plan *P, const void *x, const void *q, const void *adt, c
         auto kern = adjoint_hier<T, SOA>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
+        int *err = nullptr;
+        if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
         for (int c = 0; c < P->ncolors; ++c) {
             int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
             if (nb == 0) continue;
             kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
                                                       P->dev.tcolor, P->dev.fp, (const T *)x, (const T *)q,
                                                       (const T *)adt, (const T *)rbar, (T *)qbar, (T *)xbar, nnode,
-                                                      ncell, cap_c, cap_n, gm1, half_eps);
+                                                      ncell, cap_c, cap_n, gm1, half_eps, err);
         }
     } else {
         const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;

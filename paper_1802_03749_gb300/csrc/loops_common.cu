@@ -82,7 +82,7 @@ namespace {
 constexpr int kReduceParts = 152 * 4;  // one partial per CTA of the update grid
 std::mutex g_scratch_mu;
 double *g_partials[64] = {nullptr};
-__device__ int g_device_error;  // error word of bounded device-side waits
+int *g_error_word[64] = {nullptr};
 }  // namespace
 
 int mp_reduce_scratch(double **partials, int *nparts)
@@ -97,16 +97,32 @@ int mp_reduce_scratch(double **partials, int *nparts)
     return MP_OK;
 }
 
+int mp_device_error_word(int **word)
+{
+    int dev = 0;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return MP_EINVAL;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_error_word[dev]) {
+        MP_CUDA_TRY(cudaMalloc(&g_error_word[dev], sizeof(int)));
+        MP_CUDA_TRY(cudaMemset(g_error_word[dev], 0, sizeof(int)));
+    }
+    *word = g_error_word[dev];
+    return MP_OK;
+}
+
 extern "C" int mp_check_device_status(void *stream)
 {
+    int *w = nullptr;
+    int rc = mp_device_error_word(&w);
+    if (rc != MP_OK) return rc;
     int h = 0;
-    MP_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_device_error, sizeof(int), 0, cudaMemcpyDeviceToHost,
-                                          as_stream(stream)));
+    MP_CUDA_TRY(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, as_stream(stream)));
     MP_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
-    if (h) {
-        int zero = 0;
-        MP_CUDA_TRY(cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)));
-        return MP_ETIMEOUT;
+    if (h != MP_DEVERR_NONE) {
+        MP_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(int), as_stream(stream)));
+        MP_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+        return h == MP_DEVERR_SMEM ? MP_ESMEM : MP_ETIMEOUT;
     }
     return MP_OK;
 }

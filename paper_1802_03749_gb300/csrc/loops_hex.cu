@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
                                                 const int32_t *__restrict__ fp, const T *__restrict__ x,
                                                 const T *__restrict__ v, const T *__restrict__ sig,
                                                 T *__restrict__ f, T *__restrict__ vol, int64_t nnode,
-                                                int64_t nelem, int cap, T kappa)
+                                                int64_t nelem, int cap, T kappa, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_x = reinterpret_cast<T *>(smem_raw);  // [3][cap]
@@ -134,6 +134,11 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0];
+    if ((unsigned)(reinterpret_cast<unsigned char *>(s_gid + cap) - smem_raw) > dynamic_smem_bytes() || nn > cap ||
+        d.nitems > (int)blockDim.x) {
+        if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
+        return;
+    }
     const int32_t *fpn = fp + d.fp_start[0];
     for (int i = tid; i < nn; i += blockDim.x) {
         int g = fpn[i];
@@ -252,13 +257,15 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
         auto kern = hex_hier<T, SOA>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
+        int *err = nullptr;
+        if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
         if (P->opts.block_size > 512) return MP_EINVAL;
         for (int c = 0; c < P->ncolors; ++c) {
             int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
             if (nb == 0) continue;
             kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const uint4 *>(P->dev.lmap),
                                                       P->dev.tcolor, P->dev.fp, (const T *)x, (const T *)v,
-                                                      (const T *)sig, (T *)f, (T *)vol, nnode, nelem, cap, (T)kappa);
+                                                      (const T *)sig, (T *)f, (T *)vol, nnode, nelem, cap, (T)kappa, err);
         }
     } else {
         const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
                                                       const int32_t *__restrict__ fp, const T *__restrict__ x,
                                                       const T *__restrict__ q, const T *__restrict__ adt,
                                                       T *__restrict__ res, int64_t nnode, int64_t ncell, int cap_c,
-                                                      int cap_n, T gm1, T half_eps)
+                                                      int cap_n, T gm1, T half_eps, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_q = reinterpret_cast<T *>(smem_raw);
@@ -58,6 +58,13 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
+    // the carve-up above must fit the launch's dynamic shared memory and
+    // the block's footprint its capacity; otherwise record and return
+    if ((unsigned)(reinterpret_cast<unsigned char *>(s_gid + cap_c) - smem_raw) > dynamic_smem_bytes() ||
+        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x) {
+        if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
+        return;
+    }
     const int32_t *fpn = fp + d.fp_start[0];
     const int32_t *fpc = fp + d.fp_start[1];
 
@@ -360,13 +367,15 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         auto kern = res_calc_hier<T, SOA>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
+        int *err = nullptr;
+        if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
         const int32_t *fp = P->dev.fp;
         for (int c = 0; c < P->ncolors; ++c) {
             int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
             if (nb == 0) continue;
             kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
                                                       P->dev.tcolor, fp, (const T *)x, (const T *)q, (const T *)adt,
-                                                      (T *)res, nnode, ncell, cap_c, cap_n, gm1, half_eps);
+                                                      (T *)res, nnode, ncell, cap_c, cap_n, gm1, half_eps, err);
         }
     } else {
         const bool atomic = co == MP_COLOR_ATOMIC;

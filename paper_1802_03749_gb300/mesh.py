@@ -85,3 +85,56 @@ class HexPlan:
         out = np.empty_like(b)
         out[perm] = b
         return out
+
+
+class AirfoilStep:
+    """One explicit time step of the Airfoil-style solver on the device:
+    save_soln, adt_calc, res_calc, bres_calc, update (K = 1 stage per step).
+    Data live in plan numbering and the plans' layout; ``rms`` accumulates
+    the FP64 sum of squared updates on the device.  The step can be captured
+    in a CUDA graph (``capture``) once the plans are uploaded."""
+
+    def __init__(self, plans: AirfoilPlans, x, q, qinf, dtype="f64", gam=1.4, eps=0.05, cfl=0.9):
+        import torch
+        from . import loop_adt_calc, loop_bres_calc, loop_res_calc, loop_save_soln, loop_update  # noqa: F401
+        self.P = plans
+        self.gam, self.eps, self.cfl = gam, eps, cfl
+        self.qinf = [float(v) for v in qinf]
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        self.x = torch.tensor(plans.to_plan(x, "node"), dtype=tdt, device="cuda")
+        self.q = torch.tensor(plans.to_plan(q, "cell"), dtype=tdt, device="cuda")
+        self.qold = torch.zeros_like(self.q)
+        self.res = torch.zeros_like(self.q)
+        self.adt = torch.zeros(plans.ncell, dtype=tdt, device="cuda")
+        self.rms = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for p in (plans.res, plans.bres, plans.adt):
+            p.upload()
+        self.graph = None
+
+    def step(self):
+        from . import loop_adt_calc, loop_bres_calc, loop_res_calc, loop_save_soln, loop_update
+        P = self.P
+        loop_save_soln(self.q, self.qold, P.layout)
+        loop_adt_calc(P.adt, self.x, self.q, self.adt, self.gam, self.cfl)
+        loop_res_calc(P.res, self.x, self.q, self.adt, self.res, self.gam, self.eps)
+        loop_bres_calc(P.bres, self.x, self.q, self.adt, self.res, self.qinf, self.gam, self.eps)
+        loop_update(self.qold, self.q, self.res, self.adt, self.rms, P.layout)
+
+    def capture(self, steps_per_graph: int = 1):
+        """Capture ``steps_per_graph`` steps into one CUDA graph."""
+        import torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()                      # warm-up outside capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(steps_per_graph):
+                self.step()
+        self.graph = g
+        return g
+
+    def q_original(self):
+        return self.P.from_plan(self.q.cpu().numpy().astype("float64"), "cell", 4)

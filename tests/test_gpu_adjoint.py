@@ -59,9 +59,13 @@ def test_adjoint_dot_product_and_fd():
         rp = oracle.res_calc(m.edge2node, m.edge2cell, m.x + h * dx, q + h * dq, adt)
         rm = oracle.res_calc(m.edge2node, m.edge2cell, m.x - h * dx, q - h * dq, adt)
         fd = float((rb * (rp - rm)).sum()) / (2 * h)
-        worst_fd = max(worst_fd, abs(fd - ad) / abs(ad))
+        # FD error is set by rounding in rp - rm over the size of the summed
+        # terms, not by |ad| (which may nearly cancel): normalise by the sum
+        # of absolute terms of the adjoint dot product
+        scale = float(np.abs(qb * dq).sum() + np.abs(xb * dx).sum())
+        worst_fd = max(worst_fd, abs(fd - ad) / scale)
     assert worst_cs <= 1e-12
-    assert worst_fd <= 1e-6
+    assert worst_fd <= 1e-7
 
 
 def test_autograd_function():
