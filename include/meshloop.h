@@ -63,6 +63,8 @@ extern "C" {
 #define MP_ENOMEM (-7)     /* host allocation failed                                   */
 #define MP_EPLAN (-8)      /* plan does not fit the loop (maps, colouring, layout)     */
 #define MP_EIO (-9)        /* plan file could not be read or written                   */
+#define MP_ETOOBIG (-10)   /* size exceeds the fixed static scratch of an allocation-free
+                              entry point                                                */
 
 #define MP_MAX_BLOCK_COLORS 256  /* limit of the paper's library, Sec. 3.1.5        */
 #define MP_MAX_THREAD_COLORS 64
@@ -217,6 +219,32 @@ int loop_save_soln(int64_t ncell, int32_t dtype, int32_t layout, const void *q, 
                    void *stream);
 int loop_update(int64_t ncell, int32_t dtype, int32_t layout, const void *qold, void *q, void *res,
                 const void *adt, double *rms_dev, void *stream);
+
+/* Allocation-free variant of loop_update (the paper has no counterpart).
+ * Same arguments, results and determinism as loop_update, but its scratch
+ * (one FP64 partial sum per CTA of 256 threads) is a fixed static device
+ * array of MP_NOALLOC_MAX_PARTIALS doubles inside the library instead of
+ * memory obtained from cudaMalloc, so the call never allocates or frees
+ * device memory.  It is meant for callers that cannot allocate: host
+ * applications that reserve all device memory up front in their own pool,
+ * or that forbid device allocation (and the implicit device synchronisation
+ * cudaMalloc may cause) once they are running.
+ * Limits and behaviour:
+ *  - ncell may be at most MP_NOALLOC_MAX_CELLS (2048 cells per partial);
+ *    larger sizes return MP_ETOOBIG before anything is launched.
+ *  - The first call on each device looks up the device address of the
+ *    static array (cudaGetSymbolAddress) with that device current; make that
+ *    first call before any stream capture.
+ *  - Every device that loads the library holds the array until exit.  All
+ *    calls share it and it keeps the last call's partial sums; each call
+ *    overwrites every entry it reads, so nothing needs clearing, but calls
+ *    whose executions overlap on the GPU (other streams, other threads) race
+ *    on it: serialise them.                                                 */
+#define MP_NOALLOC_MAX_PARTIALS 4096
+#define MP_NOALLOC_CELLS_PER_PARTIAL 2048
+#define MP_NOALLOC_MAX_CELLS ((int64_t)MP_NOALLOC_MAX_PARTIALS * MP_NOALLOC_CELLS_PER_PARTIAL)
+int loop_update_noalloc(int64_t ncell, int32_t dtype, int32_t layout, const void *qold, void *q, void *res,
+                        const void *adt, double *rms_dev, void *stream);
 
 /* Hex assembly (Sec. 3.1.4's IntegrateStressForElems access pattern): over
  * hex8 elements read x, v (3 per node) on 8 nodes and sig (3, direct),

@@ -23,13 +23,14 @@ from . import _build
 
 __all__ = [
     "MeshLoopError", "Plan", "lib", "loop_res_calc", "loop_bres_calc", "loop_adt_calc", "loop_save_soln",
-    "loop_update", "loop_elem_assemble", "loop_adjoint", "mesh_map_renumber", "mp_check_device_status",
+    "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "mesh_map_renumber", "mp_check_device_status",
     "REORDER", "COLORING", "LAYOUT", "MP_MAX_BLOCK_COLORS",
 ]
 
 MP_OK = 0
 MP_ERRORS = {-1: "MP_EINVAL", -2: "MP_EMAPRANGE", -3: "MP_ECOLORS", -4: "MP_ESMEM", -5: "MP_ECUDA",
-             -6: "MP_ETIMEOUT", -7: "MP_ENOMEM", -8: "MP_EPLAN", -9: "MP_EIO"}
+             -6: "MP_ETIMEOUT", -7: "MP_ENOMEM", -8: "MP_EPLAN", -9: "MP_EIO", -10: "MP_ETOOBIG"}
+MP_NOALLOC_MAX_CELLS = 4096 * 2048
 MP_MAX_BLOCK_COLORS = 256
 MP_MAX_MAPS = 4
 MP_MAX_TOSETS = 2
@@ -98,6 +99,7 @@ SIGNATURES = {
     "loop_adt_calc": (_I32, [_P, _I32, _P, _P, _P, _D, _D, _P]),
     "loop_save_soln": (_I32, [_I64, _I32, _I32, _P, _P, _P]),
     "loop_update": (_I32, [_I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
+    "loop_update_noalloc": (_I32, [_I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     "loop_elem_assemble": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _D, _P]),
     "loop_adjoint": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P, _D, _D, _P]),
     "mp_error_string": (ctypes.c_char_p, [_I32]),
@@ -308,6 +310,18 @@ def loop_update(qold, q, res, adt, rms, layout: str = "aos", stream=None):
         raise MeshLoopError(-1, "rms must be a CUDA float64 tensor")
     _check(lib().loop_update(adt.numel(), dt, LAYOUT[layout], _ptr(qold), _ptr(q), _ptr(res), _ptr(adt),
                              _ptr(rms), _stream(stream)), "loop_update")
+
+
+def loop_update_noalloc(qold, q, res, adt, rms, layout: str = "aos", stream=None):
+    """``loop_update`` without any device allocation: the library's fixed
+    static scratch holds the partial sums (at most MP_NOALLOC_MAX_CELLS
+    cells; calls that overlap on the GPU must be serialised)."""
+    import torch
+    dt = _dtype_of(qold, q, res, adt)
+    if rms.dtype != torch.float64 or not rms.is_cuda:
+        raise MeshLoopError(-1, "rms must be a CUDA float64 tensor")
+    _check(lib().loop_update_noalloc(adt.numel(), dt, LAYOUT[layout], _ptr(qold), _ptr(q), _ptr(res), _ptr(adt),
+                                     _ptr(rms), _stream(stream)), "loop_update_noalloc")
 
 
 def loop_elem_assemble(plan: Plan, x, v, sig, f, vol, kappa: float = 0.01, stream=None):

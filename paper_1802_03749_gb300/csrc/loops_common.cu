@@ -225,3 +225,59 @@ extern "C" int loop_update(int64_t ncell, int32_t dtype, int32_t layout, const v
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
+
+// ------------------------------------------------- allocation-free update
+
+namespace {
+// Static scratch of loop_update_noalloc: one partial sum per CTA.  In host
+// code this name is only a stand-in; kernels get its device address.
+static __device__ __align__(256) double g_noalloc_partials[MP_NOALLOC_MAX_PARTIALS];
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[64] = {nullptr};
+
+// Device address of the static scratch on the current device, looked up
+// once per device with that device current.
+int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return MP_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        double *p = nullptr;
+        if (cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_partials) != cudaSuccess || !p)
+            return MP_ECUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MP_OK;
+}
+}  // namespace
+
+extern "C" int loop_update_noalloc(int64_t ncell, int32_t dtype, int32_t layout, const void *qold, void *q,
+                                   void *res, const void *adt, double *rms_dev, void *stream)
+{
+    if (ncell < 0 || (dtype != MP_F64 && dtype != MP_F32) || (layout != MP_LAYOUT_AOS && layout != MP_LAYOUT_SOA))
+        return MP_EINVAL;
+    if (ncell > MP_NOALLOC_MAX_CELLS) return MP_ETOOBIG;
+    if (ncell == 0) return MP_OK;
+    if (!qold || !q || !res || !adt || !rms_dev) return MP_EINVAL;
+    double *parts = nullptr;
+    int rc = noalloc_scratch(&parts);
+    if (rc != MP_OK) return rc;
+    // one CTA per MP_NOALLOC_CELLS_PER_PARTIAL cells: at most
+    // MP_NOALLOC_MAX_PARTIALS partials, each written before it is summed
+    const int nparts = (int)((ncell + MP_NOALLOC_CELLS_PER_PARTIAL - 1) / MP_NOALLOC_CELLS_PER_PARTIAL);
+    cudaStream_t s = as_stream(stream);
+    bool soa = layout == MP_LAYOUT_SOA;
+    if (dtype == MP_F64) {
+        auto k = soa ? update_kernel<double, true> : update_kernel<double, false>;
+        k<<<nparts, 256, 0, s>>>((const double *)qold, (double *)q, (double *)res, (const double *)adt, ncell, parts);
+    } else {
+        auto k = soa ? update_kernel<float, true> : update_kernel<float, false>;
+        k<<<nparts, 256, 0, s>>>((const float *)qold, (float *)q, (float *)res, (const float *)adt, ncell, parts);
+    }
+    sum_partials_kernel<<<1, 256, 0, s>>>(parts, nparts, rms_dev);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}

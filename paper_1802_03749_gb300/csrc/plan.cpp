@@ -956,6 +956,7 @@ const char *mp_error_string(int code)
     case MP_ENOMEM: return "host allocation failed";
     case MP_EPLAN: return "plan does not fit this loop";
     case MP_EIO: return "plan file could not be read or written";
+    case MP_ETOOBIG: return "size exceeds the fixed static scratch of an allocation-free entry point";
     default: return "unknown error";
     }
 }
