@@ -1,18 +1,18 @@
-"""Benchmark of the locality-optimised res_calc loop (and its baselines).
+"""Benchmark of the locality-optimised res_calc loop, its baselines and the
+other loops of the library, on synthetic meshes shaped like the paper's.
 
-Default workload: res_calc on a jittered, randomly renumbered 2400x1200 quad
-mesh (2.88M cells, 5.756M interior edges), FP64, through the C ABI.  A step
-is one full res_calc pass (every block colour) of the two-layer staged
-kernel on the RCM + partitioned plan.  The metric is interior edges per
-second (Gedges/s); useful bandwidth follows the paper's formula (Sec. 3.1:
-each dataset counted once, twice if read and written; maps as int32).
+Headline workload: res_calc on a jittered, randomly renumbered 2400x1200 quad
+mesh (2,880,000 cells, 5,756,400 interior edges) with FP64 data, through the
+C ABI.  A step is one full res_calc pass (every block colour) of the
+two-layer staged kernel (RCM + partition plan).  The metric is interior
+edges per second; useful bandwidth follows the paper's formula (Sec. 3.1:
+each dataset once, twice if read and written, maps as int32 datasets).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line on rank 0.  Under torchrun each rank runs an
-independent replica of the workload (replicas only; no collective on the
-data path) and the value is the total edges of all ranks over the slowest
-rank's time.
+Prints one JSON line on rank 0.  Under torchrun every rank runs an
+independent replica of the workload (no collective on the data path); the
+value is the edges of all ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -34,19 +34,33 @@ import meshgen  # noqa: E402
 METRIC = "res_calc Gedges/s & HBM GB/s % of peak: two-layer vs atomics vs global color"
 NX, NY = 2400, 1200
 GAM, EPS = 1.4, 0.05
+L2_BYTES = 129 * 10 ** 6
+
+# algorithmic floating-point operations of one interior edge as the oracle
+# evaluates it: two normal fluxes of 20 (pressure 7, normal velocity 4,
+# components 9), the normal 2, mu 3, four flux components of 5, two
+# increments of 4 components
+FLOPS_PER_EDGE = 73
+# FP64 FMA throughput of GB300: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def useful_bytes_res_calc(ncell, nnode, nedge, elt):
-    """Sec. 3.1 useful bytes: x (2/node) + q (4/cell) + adt (1/cell) read,
-    res (4/cell) read and written (w = 2), two int32 maps of 2 per edge."""
+    """x (2/node) + q (4/cell) + adt (1/cell) read, res (4/cell) read and
+    written (w = 2), two int32 maps of 2 per edge."""
     return (2 * nnode + 4 * ncell + ncell + 2 * 4 * ncell) * elt + 2 * 2 * 4 * nedge
 
 
-# algorithmic floating-point operations of one interior edge of res_calc as
-# the oracle evaluates it: two normal fluxes (20 each: pressure 7, normal
-# velocity 4, components 9), the normal 2, mu 3, four flux components 5 each,
-# and the two increments of 4 components (8)
-FLOPS_PER_EDGE = 73
+def useful_bytes_hex(nelem, nnode, elt):
+    """x, v (3/node) read, f (3/node) read and written, sig (3/elem) read,
+    vol (1/elem) written, map 8 int32 per element."""
+    return (3 * nnode + 3 * nnode + 2 * 3 * nnode + 3 * nelem + nelem) * elt + 8 * 4 * nelem
+
+
+def useful_bytes_adjoint(ncell, nnode, nedge):
+    """x, q, adt, res_bar read; q_bar (4/cell) and x_bar (2/node) read and
+    written; two int32 maps."""
+    return (2 * nnode + 4 * ncell + ncell + 4 * ncell + 2 * 4 * ncell + 2 * 2 * nnode) * 8 + 16 * nedge
 
 
 def read_peaks():
@@ -58,63 +72,90 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 FMA throughput of GB300: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-
-
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
-
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-
-    def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "100"], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        out, _ = self.proc.communicate(timeout=10)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
-
-
-def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
 def synthetic_adt(m):
     """A positive per-cell time-step field of the magnitude the free stream
     gives on an h x h cell ((2h(|u|+|v|) + 4h)/0.9, about 5.4 h)."""
     return meshgen.positive_field(m.ncell, 5.0 * m.h, 6.0 * m.h)
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons, each line stamped with the
+    host time it arrived, so that samples can be matched to a time window."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self, wait_s=3.0):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "50"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < wait_s:
+            time.sleep(0.02)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm, smax = float(f[0]), float(f[1])
+            except ValueError:
+                continue
+            reasons = [n for n, v in zip(self.NAMES, f[3:7]) if v.lower().startswith("active")]
+            self.samples.append((time.time(), sm, smax, reasons))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def window(self, t0, t1, pad=0.06):
+        s = [x for x in self.samples if t0 - pad <= x[0] <= t1 + pad]
+        kind = "timed region"
+        if not s:   # a timed region shorter than the sampling period: nearest samples
+            s = sorted(self.samples, key=lambda x: min(abs(x[0] - t0), abs(x[0] - t1)))[:2]
+            kind = "nearest samples to the timed region"
+        if not s:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median([x[1] for x in s])), "sm_max_mhz": max(x[2] for x in s),
+                "reasons": sorted({r for x in s for r in x[3]}), "samples": len(s), "window": kind}
+
+
+def dist_setup():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(ms, dist, device="cpu"):
+    """Slowest rank's time (replicas run independently; the job ends with
+    the slowest).  ``dist`` is torch.distributed or None for one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_per_step):
+    """Whole-job throughput: the units of all ranks over the slowest time."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
 
 
 def oracle_res_calc_rate(m, q, adt, budget_s):
@@ -133,7 +174,7 @@ def oracle_res_calc_rate(m, q, adt, budget_s):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    """Reference arm: the FP64 CPU oracle's res_calc on the host (1 core)."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
@@ -155,9 +196,117 @@ def run_reference(args):
             "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, FP64", "cells": m.ncell,
                        "edges": m.nedge},
             "cpu_baseline": {"value": v, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full res_calc passes ({m.nedge} edges each)"},
+                             "sample": f"{args.steps} full res_calc passes of {m.nedge} edges, 1 host core"},
             "e2e": {"value": v, "unit": "Gedges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+class Timer:
+    """CUDA-event timing of a callable on the current stream, with a
+    barrier and synchronisation on both sides and max over ranks."""
+
+    def __init__(self, torch, dist):
+        self.torch, self.dist = torch, dist
+
+    def __call__(self, fn, steps, warmup):
+        torch, dist = self.torch, self.dist
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.time()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, device="cuda")
+        return ms / steps, (t0, t1)
+
+
+def bench_rows(ml, torch, timer, args):
+    """Measurements of the other loops (not the headline): hex assembly,
+    the adjoint and the batched graph-captured time step."""
+    from paper_1802_03749_gb300 import autotune
+    from paper_1802_03749_gb300.mesh import AirfoilBatch, AirfoilPlans, AirfoilStep, HexPlan
+    hbm, _ = read_peaks()
+    rows = {}
+    # hex assembly, n^3 elements
+    hm = meshgen.hex_mesh(args.hex_n)
+    sig, v = meshgen.hex_fields(hm)
+    for dtype in ("f64", "f32"):
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        elt = 8 if dtype == "f64" else 4
+        for coloring, reorder in (("hier", "partition"), ("atomic", "rcm"), ("global", "rcm")):
+            H = HexPlan(hm.nnode, hm.elem2node, block_size=256, reorder=reorder, coloring=coloring)
+            H.plan.upload()
+            x = torch.tensor(H.to_plan(hm.x, "node"), dtype=tdt, device="cuda")
+            vd = torch.tensor(H.to_plan(v, "node"), dtype=tdt, device="cuda")
+            sd = torch.tensor(H.to_plan(sig, "elem"), dtype=tdt, device="cuda")
+            f = torch.zeros_like(x)
+            vol = torch.zeros(hm.nelem, dtype=tdt, device="cuda")
+            ms, _ = timer(lambda: ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01), 10, 2)
+            ub = useful_bytes_hex(hm.nelem, hm.nnode, elt)
+            st = H.plan.stats()
+            rows[f"hex_{dtype}_{coloring}_{reorder}"] = {
+                "workload": f"hex assembly {args.hex_n}^3 elements", "ms": ms,
+                "gelems_s": hm.nelem / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
+                "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
+                "reuse": st["reuse_all"]}
+            del x, vd, sd, f, vol
+    # adjoint, 1200x600
+    am = meshgen.quad_mesh(1200, 600)
+    aq = meshgen.quad_state(am.ncell)
+    aadt = synthetic_adt(am)
+    rb = meshgen.adjoint_seed(am.ncell)
+    for coloring, reorder in (("hier", "partition"), ("atomic", "rcm")):
+        P = AirfoilPlans(am.ncell, am.nnode, am.edge2node, am.edge2cell, am.bedge2node, am.bedge2cell, am.cell2node,
+                         block_size=384, reorder=reorder, coloring=coloring, adjoint=True)
+        P.res.upload()
+        t = lambda a, w: torch.tensor(P.to_plan(a, w), device="cuda")
+        x, qd, ad, rbd = t(am.x, "node"), t(aq, "cell"), t(aadt, "cell"), t(rb, "cell")
+        qb, xb = torch.zeros_like(qd), torch.zeros_like(x)
+        ms, _ = timer(lambda: ml.loop_adjoint(P.res, x, qd, ad, rbd, qb, xb), 10, 2)
+        ub = useful_bytes_adjoint(am.ncell, am.nnode, am.nedge)
+        rows[f"adjoint_f64_{coloring}_{reorder}"] = {
+            "workload": "res_calc adjoint 1200x600", "ms": ms, "gedges_s": am.nedge / ms / 1e6,
+            "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm}
+    # batched time step: meshes of uneven size, FP32 data, FP64 update and sum
+    sizes = meshgen.batch_sizes(args.batch)
+    meshes = [meshgen.quad_mesh(nx, ny, seed=meshgen.DEFAULT_SEED + 97 * i) for i, (nx, ny) in enumerate(sizes)]
+    states = [meshgen.quad_state(mm.ncell, seed=meshgen.DEFAULT_SEED + 97 * i) for i, mm in enumerate(meshes)]
+    adts = [synthetic_adt(mm) for mm in meshes]
+    qinf = meshgen.freestream()
+    tune_t0 = time.time()
+    tuned, choices = autotune.tune(meshes, states, adts, dtype="f32", reps=10)
+    tune_s = time.time() - tune_t0
+    B = AirfoilBatch(meshes, states, qinf, choices, dtype="f32")
+    B.capture(steps_per_graph=1)
+    ms_graph, _ = timer(lambda: B.graph.replay(), 20, 3)
+    ms_batch_eager, _ = timer(B.step, 20, 3)
+    per = [AirfoilStep(AirfoilPlans(mm.ncell, mm.nnode, mm.edge2node, mm.edge2cell, mm.bedge2node, mm.bedge2cell,
+                                    mm.cell2node, block_size=480, reorder="partition"), mm.x, s, qinf, dtype="f32")
+           for mm, s in zip(meshes, states)]
+
+    def per_mesh():
+        for S in per:
+            S.step()
+
+    ms_per, _ = timer(per_mesh, 5, 1)
+    cells = sum(mm.ncell for mm in meshes)
+    edges = sum(mm.nedge for mm in meshes)
+    rows["batch_step_f32"] = {
+        "workload": f"{args.batch} quad meshes, {cells} cells, {edges} edges, full time step, FP32 data, "
+                    "FP64 update and residual sum",
+        "ms_graph_batched": ms_graph, "ms_eager_batched": ms_batch_eager, "ms_per_mesh_launches": ms_per,
+        "speedup_vs_per_mesh": ms_per / ms_graph, "gedges_s": edges / ms_graph / 1e6,
+        "autotune": tuned, "autotune_seconds": tune_s}
+    return rows
 
 
 def main():
@@ -166,13 +315,17 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--block-size", type=int, default=480)
+    ap.add_argument("--block-size", type=int, default=384)
     ap.add_argument("--layout", default="aos", choices=["aos", "soa"])
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--compute", default="dw", choices=["dw", "f64", "f32"],
+                    help="dw: FP64 data with double-word arithmetic; f64: native FP64; f32: FP32 data")
     ap.add_argument("--no-variants", action="store_true", help="skip the baseline variants")
+    ap.add_argument("--no-rows", action="store_true", help="skip the hex / adjoint / batch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--nx", type=int, default=NX, help="quad grid size (profiling runs use smaller meshes)")
     ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--hex-n", type=int, default=120)
+    ap.add_argument("--batch", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -188,18 +341,21 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    timer = Timer(torch, dist)
 
     m = meshgen.quad_mesh(args.nx, args.ny)
     q = meshgen.quad_state(m.ncell)
     adt = synthetic_adt(m)
-    tdt = torch.float64 if args.dtype == "f64" else torch.float32
-    elt = 8 if args.dtype == "f64" else 4
+    f32 = args.compute == "f32"
+    tdt = torch.float32 if f32 else torch.float64
+    elt = 4 if f32 else 8
+    compute = "dw" if args.compute == "dw" else None
     useful = useful_bytes_res_calc(m.ncell, m.nnode, m.nedge, elt)
-    stream = torch.cuda.current_stream()
+    hbm_peak, peak_kind = read_peaks()
 
-    def setup(coloring, reorder, layout):
+    def setup(coloring, reorder, layout=args.layout, bs=args.block_size):
         P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                         block_size=args.block_size, reorder=reorder, coloring=coloring, layout=layout)
+                         block_size=bs, reorder=reorder, coloring=coloring, layout=layout)
         P.res.upload()
         d = {"x": torch.tensor(P.to_plan(m.x, "node"), dtype=tdt, device="cuda"),
              "q": torch.tensor(P.to_plan(q, "cell"), dtype=tdt, device="cuda"),
@@ -207,39 +363,24 @@ def main():
         d["res"] = torch.zeros_like(d["q"])
         return P, d
 
-    def time_steps(P, d, steps, warmup, per_launch=False):
-        for _ in range(warmup):
-            ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS)
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
-
     # ---------------------------------------------------------- headline
-    P, d = setup("hier", "partition", args.layout)
+    P, d = setup("hier", "partition")
     st = P.res.stats()
+    step = lambda: ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS, compute=compute)
     clk = ClockSampler(local)
     clk.start()
-    ms = time_steps(P, d, args.steps, args.warmup)
-    clocks = clk.stop()
-    ms_step = ms / args.steps
-    value = world * m.nedge / (ms_step * 1e-3) / 1e9
+    ms_step, (t0, t1) = timer(step, args.steps, args.warmup)
+    clocks = clk.window(t0, t1)
+    value = job_rate(m.nedge, world, ms_step) / 1e9
     gbs = useful / (ms_step * 1e-3) / 1e9
-    hbm_peak, peak_kind = read_peaks()
-    tflops = FLOPS_PER_EDGE * m.nedge / (ms_step * 1e-3) / 1e12
+    if args.compute == "f64":
+        roof = {"bound": "alu", "achieved": FLOPS_PER_EDGE * m.nedge / ms_step / 1e9, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_kind": "derived FP64 FMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
 
     # ---------------------------------------------------------- e2e (host buffers)
     hx = torch.tensor(P.to_plan(m.x, "node"), dtype=tdt).pin_memory()
@@ -247,83 +388,77 @@ def main():
     ha = torch.tensor(P.to_plan(adt, "cell"), dtype=tdt).pin_memory()
     hr = torch.zeros_like(hq).pin_memory()
     hout = torch.empty_like(hq).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
 
     def e2e_step():
         d["x"].copy_(hx, non_blocking=True)
         d["q"].copy_(hq, non_blocking=True)
         d["adt"].copy_(ha, non_blocking=True)
         d["res"].copy_(hr, non_blocking=True)
-        ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS)
+        ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS, compute=compute)
         hout.copy_(d["res"], non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_ms, _ = timer(e2e_step, max(3, min(args.steps, 20)), 2)
     h2d = (hx.numel() + hq.numel() + ha.numel() + hr.numel()) * elt
     d2h = hout.numel() * elt
+    launches = args.steps * st["nblock_colors"]
+    del d
 
     # ---------------------------------------------------------- variants
-    variants = {"two_layer_partition": {"gedges_s": value / world, "ms": ms_step, "useful_gbs": gbs,
-                                        "block_colors": st["nblock_colors"],
-                                        "thread_colors_mean": st["mean_thread_colors"],
-                                        "reuse": st["reuse_all"], "plan_seconds": st["seconds_total"]}}
-    del d
+    variants = {"two_layer_partition" + ("_dw" if compute else ""): {
+        "gedges_s": value / world, "ms": ms_step, "useful_gbs": gbs, "block_colors": st["nblock_colors"],
+        "thread_colors_mean": st["mean_thread_colors"], "reuse": st["reuse_all"],
+        "plan_seconds": st["seconds_total"]}}
     if not args.no_variants:
-        for name, (coloring, reorder) in {"two_layer_rcm": ("hier", "rcm"), "global_rcm": ("global", "rcm"),
-                                          "global_none": ("global", "none"), "atomic_rcm": ("atomic", "rcm"),
-                                          "atomic_none": ("atomic", "none")}.items():
+        ks = max(5, args.steps // 2)
+        todo = [("two_layer_rcm", "hier", "rcm", compute), ("global_rcm", "global", "rcm", None),
+                ("global_none", "global", "none", None), ("atomic_rcm", "atomic", "rcm", None),
+                ("atomic_none", "atomic", "none", None)]
+        if compute == "dw":
+            todo.insert(0, ("two_layer_partition_native_f64", "hier", "partition", None))
+        for name, coloring, reorder, comp in todo:
             try:
-                Pv, dv = setup(coloring, reorder, args.layout)
+                Pv, dv = setup(coloring, reorder)
             except ml.MeshLoopError as e:
                 variants[name] = {"error": str(e)}
                 continue
-            msv = time_steps(Pv, dv, max(5, args.steps // 2), 2) / max(5, args.steps // 2)
-            sv = Pv.res.stats()
-            variants[name] = {"gedges_s": m.nedge / (msv * 1e-3) / 1e9, "ms": msv,
-                              "useful_gbs": useful / (msv * 1e-3) / 1e9, "colors": sv["nblock_colors"]}
+            fn = lambda: ml.loop_res_calc(Pv.res, dv["x"], dv["q"], dv["adt"], dv["res"], GAM, EPS, compute=comp)
+            msv, _ = timer(fn, ks, 2)
+            variants[name] = {"gedges_s": m.nedge / msv / 1e6, "ms": msv, "useful_gbs": useful / msv / 1e6,
+                              "colors": Pv.res.stats()["nblock_colors"]}
             del dv, Pv
+
+    rows = None if args.no_rows else bench_rows(ml, torch, timer, args)
+    clk.stop()
 
     # ---------------------------------------------------------- CPU baseline (oracle)
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
         r, n, dt = oracle_res_calc_rate(m, q, adt, args.cpu_seconds)
         cpu = {"value": r, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} full res_calc passes of the same mesh ({m.nedge} edges) in {dt:.1f} s"}
+               "sample": f"{n} full FP64 res_calc passes of the same mesh ({m.nedge} edges), {dt:.1f} s on 1 core"}
 
     if rank == 0:
+        dtype = {"dw": "f64dw", "f64": "f64", "f32": "f32"}[args.compute]
         line = {
             "metric": METRIC, "value": value, "unit": "Gedges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, two-layer colouring, "
-                                   f"RCM + partition, block {args.block_size}, {args.layout.upper()}",
-                       "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (useful bytes %.0f MB > 129 MB)" % (useful / 1e6)},
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, "
+                                   + ("FP32 data" if f32 else "FP64 data")
+                                   + (", double-word arithmetic" if compute else "")
+                                   + f", two-layer colouring, RCM + partition, block {args.block_size}, "
+                                   + args.layout.upper(),
+                       "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge, "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 (useful bytes {useful / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB)"},
             "useful_gbs": gbs, "useful_frac_hbm": gbs / hbm_peak,
-            "roofline": {"bound": "alu" if args.dtype == "f64" else "hbm",
-                         "achieved": tflops if args.dtype == "f64" else gbs,
-                         "peak": FP64_PEAK_TFLOPS if args.dtype == "f64" else hbm_peak,
-                         "unit": "TFLOP/s" if args.dtype == "f64" else "GB/s",
-                         "frac": (tflops / FP64_PEAK_TFLOPS) if args.dtype == "f64" else gbs / hbm_peak,
-                         "traffic": None,
-                         "peak_kind": "derived FP64 FMA rate" if args.dtype == "f64" else peak_kind},
-            "cpu_baseline": cpu,
-            "e2e": {"value": world * m.nedge / e2e_s / 1e9, "unit": "Gedges/s", "h2d_bytes_per_step": h2d,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * m.nedge / e2e_ms / 1e6, "unit": "Gedges/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * st["nblock_colors"],
-            "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks,
             "plan": {"blocks": st["nblocks"], "block_colors": st["nblock_colors"],
                      "thread_colors_max": st["max_thread_colors"], "reuse": st["reuse_all"],
                      "plan_seconds": st["seconds_total"]},
-            "variants": variants,
+            "variants": variants, "rows": rows,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

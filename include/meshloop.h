@@ -75,7 +75,10 @@ extern "C" {
 enum { MP_REORDER_NONE = 0, MP_REORDER_RCM = 1, MP_REORDER_PARTITION = 2 };
 enum { MP_COLOR_HIER = 0, MP_COLOR_GLOBAL = 1, MP_COLOR_ATOMIC = 2 };
 enum { MP_LAYOUT_AOS = 0, MP_LAYOUT_SOA = 1 };
-enum { MP_F64 = 0, MP_F32 = 1 };
+enum { MP_F64 = 0, MP_F32 = 1, MP_F64_DW = 2 };
+/* MP_F64_DW: FP64 data, arithmetic in double-word (pairs of FP32, ~48-bit
+ * significand) on the FP32 pipes; results agree with FP64 to ~1e-13
+ * relative.  Offered by loop_res_calc with HIER plans.                   */
 
 /* One map of the loop: from the loop's iteration set (set id 0) to the
  * caller's set `to_set` (ids >= 1; maps with the same id share a to-set).
@@ -172,6 +175,18 @@ int mesh_plan_table(const mp_plan *plan, int32_t table, int32_t arg, int32_t *ou
 int mesh_map_renumber(const int32_t *idx, int64_t from_size, int32_t arity, const int32_t *from_perm,
                       const int32_t *to_perm, int64_t to_size, int32_t *out);
 
+/* Fuse the HIER plans of n meshes of one loop (same maps, AoS layout) into
+ * one plan over their disjoint union, for batched execution: the data of
+ * mesh k follow those of meshes 0..k-1 in every set (concatenated arrays,
+ * each mesh in its own plan numbering).  The fused block-descriptor table
+ * groups every mesh's blocks by colour, so a loop call on the fused plan
+ * runs the whole batch with one launch per colour phase.  Meshes keep their
+ * own block size, reordering and colouring; launches use the largest block
+ * size.  mesh_plan_perm on the fused plan returns the concatenated
+ * permutations (offset by the mesh's base).  The inputs are not retained.
+ * Errors: MP_EINVAL (a plan is not HIER/AoS or the maps differ), MP_ENOMEM.*/
+int mesh_batch_build(const mp_plan *const *plans, int32_t n, mp_plan **out);
+
 /* Copy the plan's tables to the current device (synchronous).  Idempotent.*/
 int mesh_plan_upload(mp_plan *plan);
 
@@ -189,11 +204,28 @@ int mesh_plan_load(const char *path, mp_plan **out);
  * The plan must have maps {edge->node (arity 2), edge->cell (arity 2,
  * written)} in this order; edge->node may be marked written (the adjoint's
  * plan, so that forward and adjoint share one numbering).  The colouring of the plan selects the variant:
- * HIER (staged two-layer, the product), GLOBAL or ATOMIC.
+ * HIER (staged two-layer, the product), GLOBAL or ATOMIC.  dtype MP_F64,
+ * MP_F32, or MP_F64_DW (HIER plans only; FP64 data, double-word arithmetic).
  * x: [nodes][2], q: [cells][4], adt: [cells], res: [cells][4] (AoS; SoA
  * transposes each).  stream is a cudaStream_t.                          */
 int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                   void *res, double gam, double eps, void *stream);
+
+/* Implementations of the staged two-layer (HIER) loops (res_calc; hex
+ * assembly follows SIMPLE or SMEM_ATOMIC, PIPELINED meaning SIMPLE there):
+ *  MP_STAGED_SIMPLE (default): Algorithm 1 as printed, one block per CTA
+ *    (with res prefetched at staging, so the write-back is a store);
+ *  MP_STAGED_PIPELINED: persistent CTAs walk several blocks of a colour, and
+ *    asynchronous copies (cp.async) stage block k+1's footprint while block
+ *    k is computed (res_calc FP64/FP32, blocks of at most 512 threads whose
+ *    two stages fit shared memory; other plans run SIMPLE);
+ *  MP_STAGED_SMEM_ATOMIC: as SIMPLE, but the increments go to shared memory
+ *    with atomic adds instead of one pass per thread colour (one barrier;
+ *    the order of the additions, and so the rounding, is not fixed).
+ * Block colouring still orders the write-back in every variant.
+ * Process-wide setting; returns MP_EINVAL for an unknown value.           */
+enum { MP_STAGED_PIPELINED = 0, MP_STAGED_SIMPLE = 1, MP_STAGED_SMEM_ATOMIC = 2 };
+int mp_set_staged_variant(int32_t variant);
 
 /* Far-field boundary flux bres_calc over boundary edges: with
  * q_b = (q_c + qinf)/2,  res[c] += F(q_b).n + eps adt_c (q_c - qinf).

@@ -37,7 +37,7 @@ MP_MAX_TOSETS = 2
 REORDER = {"none": 0, "rcm": 1, "partition": 2}
 COLORING = {"hier": 0, "global": 1, "atomic": 2}
 LAYOUT = {"aos": 0, "soa": 1}
-DTYPE = {"f64": 0, "f32": 1}
+DTYPE = {"f64": 0, "f32": 1, "f64dw": 2}
 TABLES = {"block_offsets": 0, "color_offsets": 1, "block_color": 2, "thread_color": 3, "map": 4,
           "footprint": 5, "fp_start": 6, "fp_count": 7, "local_map": 8}
 
@@ -92,6 +92,7 @@ SIGNATURES = {
     "mesh_plan_table": (_I32, [_P, _I32, _I32, _P, _I64, ctypes.POINTER(_I64)]),
     "mesh_map_renumber": (_I32, [_P, _I64, _I32, _P, _P, _I64, _P]),
     "mesh_plan_upload": (_I32, [_P]),
+    "mesh_batch_build": (_I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)]),
     "mesh_plan_save": (_I32, [_P, ctypes.c_char_p]),
     "mesh_plan_load": (_I32, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "loop_res_calc": (_I32, [_P, _I32, _P, _P, _P, _P, _D, _D, _P]),
@@ -105,6 +106,7 @@ SIGNATURES = {
     "mp_error_string": (ctypes.c_char_p, [_I32]),
     "mp_check_device_status": (_I32, [_P]),
     "mp_version": (ctypes.c_char_p, []),
+    "mp_set_staged_variant": (_I32, [_I32]),
 }
 
 
@@ -174,6 +176,14 @@ class Plan:
         _check(L.mesh_plan_build(arr, n, int(from_size), ctypes.byref(o), ctypes.byref(self._h)),
                "mesh_plan_build")
         self.maps_meta = [(int(m["to_set"]), int(m["to_size"])) for m in maps]
+
+    @classmethod
+    def batch(cls, plans) -> "Plan":
+        """Fuse HIER plans of several meshes (``mesh_batch_build``)."""
+        arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+        h = ctypes.c_void_p()
+        _check(lib().mesh_batch_build(arr, len(plans), ctypes.byref(h)), "mesh_batch_build")
+        return cls(None, 0, _handle=h)
 
     @classmethod
     def load(cls, path: str) -> "Plan":
@@ -276,8 +286,14 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
-def loop_res_calc(plan: Plan, x, q, adt, res, gam: float = 1.4, eps: float = 0.05, stream=None):
+def loop_res_calc(plan: Plan, x, q, adt, res, gam: float = 1.4, eps: float = 0.05, stream=None,
+                  compute: str | None = None):
+    """``compute="dw"`` selects double-word arithmetic on FP64 data (HIER plans)."""
     dt = _dtype_of(x, q, adt, res)
+    if compute == "dw":
+        if dt != DTYPE["f64"]:
+            raise MeshLoopError(-1, "double-word arithmetic needs float64 data")
+        dt = DTYPE["f64dw"]
     _check(lib().loop_res_calc(plan.handle, dt, _ptr(x), _ptr(q), _ptr(adt), _ptr(res), gam, eps,
                                _stream(stream)), "loop_res_calc")
 
@@ -335,6 +351,14 @@ def loop_adjoint(plan: Plan, x, q, adt, res_bar, q_bar, x_bar, gam: float = 1.4,
     dt = _dtype_of(x, q, adt, res_bar, q_bar, x_bar)
     _check(lib().loop_adjoint(plan.handle, dt, _ptr(x), _ptr(q), _ptr(adt), _ptr(res_bar), _ptr(q_bar),
                               _ptr(x_bar), gam, eps, _stream(stream)), "loop_adjoint")
+
+
+STAGED = {"pipelined": 0, "simple": 1, "smem_atomic": 2}
+
+
+def mp_set_staged_variant(variant: str):
+    """Select the staged two-layer implementation ("pipelined", "simple" or "smem_atomic")."""
+    _check(lib().mp_set_staged_variant(STAGED[variant]), "mp_set_staged_variant")
 
 
 def mp_check_device_status(stream=None):

@@ -46,16 +46,30 @@ int mp_device_error_word(int **word);
 // Uploads the plan's tables to the current device if not done yet.
 int mp_plan_ensure_device(const mp_plan *plan);
 
+// Pipelined persistent two-layer res_calc (FP64 / FP32).
+int mp_res_calc_pipe(const mp_plan *P, int32_t dtype, const void *x, const void *q, const void *adt, void *res,
+                     double gam, double eps, void *stream);
+// Current staged-kernel variant (mp_set_staged_variant).
+int mp_staged_variant();
+
+// Two-layer res_calc with FP64 data and double-word arithmetic.
+int mp_res_calc_dw(const mp_plan *P, const void *x, const void *q, const void *adt, void *res, double gam, double eps,
+                   void *stream);
+
 // Library-owned device scratch for deterministic reductions (per device).
 int mp_reduce_scratch(double **partials, int *nparts);
 
-// Sets the max dynamic smem attribute of a kernel once.
+// Lets a kernel use `bytes` of dynamic shared memory: the opt-in limit
+// (227 KB per CTA) minus the kernel's static shared memory.
 template <typename K>
 inline int mp_allow_smem(K kernel, int bytes)
 {
-    if (bytes > MP_SMEM_LIMIT) return MP_ESMEM;
-    if (bytes > 48 * 1024) {
-        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT) != cudaSuccess)
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return MP_ECUDA;
+    const int limit = MP_SMEM_LIMIT - (int)fa.sharedSizeBytes;
+    if (bytes > limit) return MP_ESMEM;
+    if (bytes > 48 * 1024 && fa.maxDynamicSharedSizeBytes < bytes) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
             return MP_ECUDA;
     }
     return MP_OK;

@@ -68,9 +68,9 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
     T *s_H = s_p + cap_c;
     T *s_ri = s_H + cap_c;
     T *s_rb = s_ri + cap_c;   // [4][cap_c]
-    T *s_qi = s_rb + 4 * cap_c;  // [4][cap_c] q_bar increments
+    T *s_qi = s_rb + 4 * cap_c;  // [4][cap_c] q_bar (prefetched, incremented)
     T *s_x = s_qi + 4 * cap_c;   // [2][cap_n]
-    T *s_xi = s_x + 2 * cap_n;   // [2][cap_n] x_bar increments
+    T *s_xi = s_x + 2 * cap_n;   // [2][cap_n] x_bar (prefetched, incremented)
     int *s_gc = reinterpret_cast<int *>(s_xi + 2 * cap_n);
     int *s_gn = s_gc + cap_c;
 
@@ -84,6 +84,15 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
     }
     const int32_t *fpn = fp + d.fp_start[0];
     const int32_t *fpc = fp + d.fp_start[1];
+    const bool active = tid < d.nitems;
+    ushort4 l = make_ushort4(0, 0, 0, 0);
+    int my_color = -1;
+    if (active) {  // independent of the staging: issued first
+        l = lmap[d.item_start + tid];
+        my_color = tcolor[d.item_start + tid];
+    }
+    // stage q, adt, res_bar, primitives and the current q_bar / x_bar
+    // (increments accumulate onto them; the write-back is a plain store)
     for (int i = tid; i < nc; i += blockDim.x) {
         int64_t g = fpc[i];
         T qq[4], rb[4];
@@ -92,6 +101,7 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
             int64_t j = SOA ? k * ncell + g : 4 * g + k;
             qq[k] = q[j];
             rb[k] = rbar[j];
+            s_qi[k * cap_c + i] = qbar[j];
         }
         T ri = T(1) / qq[0];
         T u = qq[1] * ri, v = qq[2] * ri;
@@ -100,7 +110,6 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
         for (int k = 0; k < 4; ++k) {
             s_q[k * cap_c + i] = qq[k];
             s_rb[k * cap_c + i] = rb[k];
-            s_qi[k * cap_c + i] = T(0);
         }
         s_adt[i] = adt[g];
         s_u[i] = u;
@@ -114,22 +123,18 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
         int64_t g = fpn[i];
         s_x[i] = SOA ? x[g] : x[2 * g];
         s_x[cap_n + i] = SOA ? x[nnode + g] : x[2 * g + 1];
-        s_xi[i] = T(0);
-        s_xi[cap_n + i] = T(0);
+        s_xi[i] = SOA ? xbar[g] : xbar[2 * g];
+        s_xi[cap_n + i] = SOA ? xbar[nnode + g] : xbar[2 * g + 1];
         s_gn[i] = (int)g;
     }
     __syncthreads();
-    const bool active = tid < d.nitems;
-    int na = 0, nb = 0, c1 = 0, c2 = 0, my_color = -1;
+    int na = 0, nb = 0, c1 = 0, c2 = 0;
     T qb1[4], qb2[4], nbx = T(0), nby = T(0);
     if (active) {
-        const int it = d.item_start + tid;
-        const ushort4 l = lmap[it];
         na = l.x;
         nb = l.y;
         c1 = l.z;
         c2 = l.w;
-        my_color = tcolor[it];
         T nx = s_x[cap_n + na] - s_x[cap_n + nb];
         T ny = s_x[nb] - s_x[na];
         T fb[4], h[4];
@@ -169,13 +174,13 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             int64_t j = SOA ? k * ncell + g : 4 * g + k;
-            qbar[j] += s_qi[k * cap_c + i];
+            qbar[j] = s_qi[k * cap_c + i];
         }
     }
     for (int i = tid; i < nn; i += blockDim.x) {
         int64_t g = s_gn[i];
-        xbar[SOA ? g : 2 * g] += s_xi[i];
-        xbar[SOA ? nnode + g : 2 * g + 1] += s_xi[cap_n + i];
+        xbar[SOA ? g : 2 * g] = s_xi[i];
+        xbar[SOA ? nnode + g : 2 * g + 1] = s_xi[cap_n + i];
     }
 }
 

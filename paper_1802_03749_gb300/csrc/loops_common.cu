@@ -51,7 +51,13 @@ int mp_plan_ensure_device(const mp_plan *cplan)
     if (P->opts.coloring == MP_COLOR_HIER) {
         if ((rc = upload(&d.desc, P->desc.data(), P->desc.size(), bytes)) != MP_OK) goto fail;
         if ((rc = upload(&d.lmap, P->lmap.data(), P->lmap.size(), bytes)) != MP_OK) goto fail;
-        if ((rc = upload(&d.tcolor, P->thread_color.data(), P->thread_color.size(), bytes)) != MP_OK) goto fail;
+        {
+            // padded to whole 16-byte words: the pipelined kernels copy the
+            // colours of a block as 4-byte words that may run past the end
+            std::vector<uint8_t> tc(P->thread_color);
+            tc.resize(((tc.size() + 4) + 15) / 16 * 16, 0);
+            if ((rc = upload(&d.tcolor, tc.data(), tc.size(), bytes)) != MP_OK) goto fail;
+        }
         {
             std::vector<int32_t> all;
             for (int s = 0; s < P->ntosets; ++s) all.insert(all.end(), P->fp_ids[s].begin(), P->fp_ids[s].end());
@@ -281,3 +287,19 @@ extern "C" int loop_update_noalloc(int64_t ncell, int32_t dtype, int32_t layout,
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
+
+// ------------------------------------------------------ staged variant
+
+namespace {
+int g_staged_variant = MP_STAGED_SIMPLE;
+}
+
+extern "C" int mp_set_staged_variant(int32_t variant)
+{
+    if (variant != MP_STAGED_PIPELINED && variant != MP_STAGED_SIMPLE && variant != MP_STAGED_SMEM_ATOMIC)
+        return MP_EINVAL;
+    g_staged_variant = variant;
+    return MP_OK;
+}
+
+int mp_staged_variant() { return g_staged_variant; }

@@ -110,14 +110,14 @@ __device__ __forceinline__ void load3(const T *__restrict__ p, int64_t n, int64_
     }
 }
 
-// smem per footprint node: x[3], v[3], f increments[3] and the global id
+// smem per footprint node: x[3], v[3], f (prefetched, incremented)[3] and the global id
 template <typename T>
 __host__ __device__ constexpr int hex_smem_per_node()
 {
     return 9 * (int)sizeof(T) + 4;
 }
 
-template <typename T, bool SOA>
+template <typename T, bool SOA, bool SMEM_ATOMIC>
 __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict__ desc, int block0,
                                                 const uint4 *__restrict__ lmap, const uint8_t *__restrict__ tcolor,
                                                 const int32_t *__restrict__ fp, const T *__restrict__ x,
@@ -140,6 +140,15 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         return;
     }
     const int32_t *fpn = fp + d.fp_start[0];
+    const bool active = tid < d.nitems;
+    uint4 l = make_uint4(0, 0, 0, 0);
+    int my_color = -1;
+    if (active) {  // independent of the staging: issued first
+        l = lmap[d.item_start + tid];
+        my_color = tcolor[d.item_start + tid];
+    }
+    // stage x, v and the current f (increments accumulate onto it; blocks of
+    // one colour share no node, so the write-back is a plain store)
     for (int i = tid; i < nn; i += blockDim.x) {
         int g = fpn[i];
         T a, b, c;
@@ -151,19 +160,17 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         s_v[i] = a;
         s_v[cap + i] = b;
         s_v[2 * cap + i] = c;
-        s_f[i] = T(0);
-        s_f[cap + i] = T(0);
-        s_f[2 * cap + i] = T(0);
+        load3<T, SOA>(f, nnode, g, a, b, c);
+        s_f[i] = a;
+        s_f[cap + i] = b;
+        s_f[2 * cap + i] = c;
         s_gid[i] = g;
     }
     __syncthreads();
-    const bool active = tid < d.nitems;
     T fe[8][3];
     int loc[8];
-    int my_color = -1;
     if (active) {
         const int e = d.item_start + tid;
-        const uint4 l = lmap[e];
         loc[0] = l.x & 0xffff;
         loc[1] = l.x >> 16;
         loc[2] = l.y & 0xffff;
@@ -172,7 +179,6 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         loc[5] = l.z >> 16;
         loc[6] = l.w & 0xffff;
         loc[7] = l.w >> 16;
-        my_color = tcolor[e];
         T xe[8][3], ve[8][3];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -186,21 +192,31 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
         vol[e] = V;
     }
-    for (int c = 0; c < d.ncolors; ++c) {
-        if (my_color == c) {
+    if (SMEM_ATOMIC) {  // shared-memory atomics instead of thread colours
+        if (active) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) s_f[a * cap + loc[i]] += fe[i][a];
+                for (int a = 0; a < 3; ++a) atomicAdd(s_f + a * cap + loc[i], fe[i][a]);
         }
         __syncthreads();
+    } else {
+        for (int c = 0; c < d.ncolors; ++c) {
+            if (my_color == c) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) s_f[a * cap + loc[i]] += fe[i][a];
+            }
+            __syncthreads();
+        }
     }
     for (int i = tid; i < nn; i += blockDim.x) {
         int64_t g = s_gid[i];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             int64_t j = SOA ? a * nnode + g : 3 * g + a;
-            f[j] += s_f[a * cap + i];
+            f[j] = s_f[a * cap + i];
         }
     }
 }
@@ -254,7 +270,7 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
     if (P->opts.coloring == MP_COLOR_HIER) {
         const int cap = P->stats.footprint_max[0];
         const int smem = cap * hex_smem_per_node<T>();
-        auto kern = hex_hier<T, SOA>;
+        auto kern = mp_staged_variant() == MP_STAGED_SMEM_ATOMIC ? hex_hier<T, SOA, true> : hex_hier<T, SOA, false>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
         int *err = nullptr;

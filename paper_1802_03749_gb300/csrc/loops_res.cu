@@ -21,7 +21,7 @@ namespace {
 
 // Dynamic shared memory layout for a block with cap_c cells and cap_n nodes:
 //   T  q[4][cap_c], adt[cap_c], u[cap_c], v[cap_c], p[cap_c], H[cap_c]
-//   T  inc[4][cap_c]
+//   T  inc[4][cap_c]         (res prefetched at staging, increments added on)
 //   T  xh[2][cap_n]          (half coordinates, n/2 = differences of these)
 //   int gid[cap_c]
 template <typename T>
@@ -36,6 +36,30 @@ __host__ __device__ constexpr int res_smem_per_node()
 }
 
 template <typename T, bool SOA>
+__device__ __forceinline__ void load_res(const T *__restrict__ res, int64_t ncell, int g, T &r0, T &r1, T &r2, T &r3)
+{
+    if (SOA) {
+        r0 = res[g];
+        r1 = res[ncell + g];
+        r2 = res[2 * ncell + g];
+        r3 = res[3 * ncell + g];
+    } else if (sizeof(T) == 8) {
+        const double2 *p = reinterpret_cast<const double2 *>(res) + 2 * (int64_t)g;
+        double2 a = p[0], b = p[1];
+        r0 = (T)a.x;
+        r1 = (T)a.y;
+        r2 = (T)b.x;
+        r3 = (T)b.y;
+    } else {
+        float4 a = reinterpret_cast<const float4 *>(res)[g];
+        r0 = (T)a.x;
+        r1 = (T)a.y;
+        r2 = (T)a.z;
+        r3 = (T)a.w;
+    }
+}
+
+template <typename T, bool SOA, bool SMEM_ATOMIC>
 __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__restrict__ desc, int block0,
                                                       const ushort4 *__restrict__ lmap,
                                                       const uint8_t *__restrict__ tcolor,
@@ -67,8 +91,17 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     }
     const int32_t *fpn = fp + d.fp_start[0];
     const int32_t *fpc = fp + d.fp_start[1];
+    // the thread's own local map and colour do not depend on the staging:
+    // issue their loads first so they overlap it
+    const bool active = tid < d.nitems;
+    ushort4 l = make_ushort4(0, 0, 0, 0);
+    int my_color = -1;
+    if (active) {
+        l = lmap[d.item_start + tid];
+        my_color = tcolor[d.item_start + tid];
+    }
 
-    // stage cells: q, adt and per-cell primitives; zero the increments
+    // stage cells: q, adt, per-cell primitives and the current res
     for (int i = tid; i < nc; i += blockDim.x) {
         int g = fpc[i];
         T r, ru, rv, E;
@@ -102,10 +135,15 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         s_v[i] = v;
         s_p[i] = p;
         s_H[i] = H;
-        s_inc[i] = T(0);
-        s_inc[cap_c + i] = T(0);
-        s_inc[2 * cap_c + i] = T(0);
-        s_inc[3 * cap_c + i] = T(0);
+        // res is prefetched here: increments accumulate onto it in shared
+        // memory and the write-back is a plain store (blocks of one colour
+        // share no cell, so no other block touches these values meanwhile)
+        T r0, r1, r2, r3;
+        load_res<T, SOA>(res, ncell, g, r0, r1, r2, r3);
+        s_inc[i] = r0;
+        s_inc[cap_c + i] = r1;
+        s_inc[2 * cap_c + i] = r2;
+        s_inc[3 * cap_c + i] = r3;
         s_gid[i] = g;
     }
     // stage nodes as half coordinates (exact scaling by 1/2)
@@ -129,13 +167,9 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     }
     __syncthreads();
 
-    const bool active = tid < d.nitems;
     T f[4] = {T(0), T(0), T(0), T(0)};
-    int c1 = 0, c2 = 0, my_color = -1;
+    int c1 = 0, c2 = 0;
     if (active) {
-        const int it = d.item_start + tid;
-        const ushort4 l = lmap[it];
-        my_color = tcolor[it];
         const int na = l.x, nb = l.y;
         c1 = l.z;
         c2 = l.w;
@@ -145,40 +179,42 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
                   s_p[c1], s_H[c1], s_adt[c1], s_q[c2], s_q[cap_c + c2], s_q[2 * cap_c + c2], s_q[3 * cap_c + c2],
                   s_u[c2], s_v[c2], s_p[c2], s_H[c2], s_adt[c2], half_eps, f);
     }
-    // thread-coloured increments in shared memory (Algorithm 1)
-    for (int c = 0; c < d.ncolors; ++c) {
-        if (my_color == c) {
+    if (SMEM_ATOMIC) {
+        // shared-memory atomics instead of thread colours: one barrier
+        if (active) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                s_inc[k * cap_c + c1] += f[k];
-                s_inc[k * cap_c + c2] -= f[k];
+                atomicAdd(s_inc + k * cap_c + c1, f[k]);
+                atomicAdd(s_inc + k * cap_c + c2, -f[k]);
             }
         }
         __syncthreads();
+    } else {
+        // thread-coloured increments in shared memory (Algorithm 1)
+        for (int c = 0; c < d.ncolors; ++c) {
+            if (my_color == c) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    s_inc[k * cap_c + c1] += f[k];
+                    s_inc[k * cap_c + c2] -= f[k];
+                }
+            }
+            __syncthreads();
+        }
     }
-    // one coalesced read-add-write per footprint cell
+    // one coalesced store per footprint cell
     for (int i = tid; i < nc; i += blockDim.x) {
         int g = s_gid[i];
         if (SOA) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) res[k * ncell + g] += s_inc[k * cap_c + i];
+            for (int k = 0; k < 4; ++k) res[k * ncell + g] = s_inc[k * cap_c + i];
         } else if (sizeof(T) == 8) {
             double2 *r2 = reinterpret_cast<double2 *>(res) + 2 * (int64_t)g;
-            double2 a = r2[0], b = r2[1];
-            a.x += (double)s_inc[i];
-            a.y += (double)s_inc[cap_c + i];
-            b.x += (double)s_inc[2 * cap_c + i];
-            b.y += (double)s_inc[3 * cap_c + i];
-            r2[0] = a;
-            r2[1] = b;
+            r2[0] = make_double2((double)s_inc[i], (double)s_inc[cap_c + i]);
+            r2[1] = make_double2((double)s_inc[2 * cap_c + i], (double)s_inc[3 * cap_c + i]);
         } else {
-            float4 *r4 = reinterpret_cast<float4 *>(res) + g;
-            float4 a = *r4;
-            a.x += (float)s_inc[i];
-            a.y += (float)s_inc[cap_c + i];
-            a.z += (float)s_inc[2 * cap_c + i];
-            a.w += (float)s_inc[3 * cap_c + i];
-            *r4 = a;
+            reinterpret_cast<float4 *>(res)[g] = make_float4((float)s_inc[i], (float)s_inc[cap_c + i],
+                                                              (float)s_inc[2 * cap_c + i], (float)s_inc[3 * cap_c + i]);
         }
     }
 }
@@ -364,7 +400,8 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         if (P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
         const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
         const int smem = cap_c * res_smem_per_cell<T>() + cap_n * res_smem_per_node<T>();
-        auto kern = res_calc_hier<T, SOA>;
+        auto kern = mp_staged_variant() == MP_STAGED_SMEM_ATOMIC ? res_calc_hier<T, SOA, true>
+                                                                 : res_calc_hier<T, SOA, false>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
         int *err = nullptr;
@@ -432,7 +469,7 @@ bool data_ok(std::initializer_list<const void *> ptrs)
 extern "C" int loop_res_calc(const mp_plan *P, int32_t dtype, const void *x, const void *q, const void *adt,
                              void *res, double gam, double eps, void *stream)
 {
-    if (!P || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
+    if (!P || (dtype != MP_F64 && dtype != MP_F32 && dtype != MP_F64_DW)) return MP_EINVAL;
     // edge->node may be marked written: an adjoint plan (both maps coloured)
     // also runs the forward loop in the same numbering
     if (!check_maps(P, 2, 0, 2, 1) && !check_maps(P, 2, 1, 2, 1)) return MP_EPLAN;
@@ -440,6 +477,11 @@ extern "C" int loop_res_calc(const mp_plan *P, int32_t dtype, const void *x, con
     if (!data_ok({x, q, adt, res})) return MP_EINVAL;
     int rc = mp_plan_ensure_device(P);
     if (rc != MP_OK) return rc;
+    if (dtype == MP_F64_DW) return mp_res_calc_dw(P, x, q, adt, res, gam, eps, stream);
+    if (P->opts.coloring == MP_COLOR_HIER && mp_staged_variant() == MP_STAGED_PIPELINED) {
+        rc = mp_res_calc_pipe(P, dtype, x, q, adt, res, gam, eps, stream);
+        if (rc != MP_EPLAN) return rc;  // otherwise the layout does not fit: one block per CTA
+    }
     cudaStream_t s = as_stream(stream);
     bool soa = P->opts.layout == MP_LAYOUT_SOA;
     if (dtype == MP_F64)

@@ -63,3 +63,21 @@ def test_hex_block_sizes_ragged(block_size):
     fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
     f, vol, H = run_hex(m, sig, v, "hier", "partition", "aos", "f64", block_size=block_size)
     assert rel_l2(f, fr) <= 1e-12 and rel_l2(vol, vr) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hex_smem_atomic_variant(dtype):
+    import paper_1802_03749_gb300 as ml
+    m, sig, v = case(14)
+    ml.mp_set_staged_variant("smem_atomic")
+    try:
+        f, vol, _ = run_hex(m, sig, v, "hier", "partition", "aos", dtype)
+    finally:
+        ml.mp_set_staged_variant("simple")
+    if dtype == "f64":
+        fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
+        assert rel_l2(f, fr) <= 1e-12
+    else:
+        fr, vr = oracle.hex_force(m.elem2node, round_to(m.x, np.float32), round_to(v, np.float32),
+                                  round_to(sig, np.float32))
+        assert rel_l2(f, fr) <= 1e-5

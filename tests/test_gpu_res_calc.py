@@ -95,3 +95,65 @@ def test_res_calc_tiny_and_empty(ml):
     z = torch.zeros(16, dtype=torch.float64, device="cuda")
     ml.loop_res_calc(P, z, z, z, z)
     assert P.stats()["nblocks"] == 0
+
+
+def run_dw(ml, m, q, adt, reorder, layout, block_size=480, res0=None):
+    from paper_1802_03749_gb300.mesh import AirfoilPlans
+    P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
+                     block_size=block_size, reorder=reorder, coloring="hier", layout=layout)
+    x = torch.tensor(P.to_plan(m.x, "node"), device="cuda")
+    qd = torch.tensor(P.to_plan(q, "cell"), device="cuda")
+    ad = torch.tensor(P.to_plan(adt, "cell"), device="cuda")
+    res = torch.tensor(P.to_plan(np.zeros_like(q) if res0 is None else res0, "cell"), device="cuda")
+    ml.loop_res_calc(P.res, x, qd, ad, res, compute="dw")
+    ml.mp_check_device_status()
+    return P.from_plan(res.cpu().numpy(), "cell", 4)
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("reorder", ["none", "rcm", "partition"])
+def test_res_calc_double_word_parity(ml, reorder, layout):
+    """FP64 data with double-word arithmetic: within the FP64 bar."""
+    m, q, adt = case(200, 100)
+    r0 = 0.01 * np.cos(np.arange(q.size)).reshape(q.shape)
+    got = run_dw(ml, m, q, adt, reorder, layout, res0=r0)
+    ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt, res=r0.copy())
+    assert rel_l2(got - r0, ref - r0) <= 1e-12
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("compute", [None, "dw"])
+def test_res_calc_full_size_parity(ml, compute):
+    """The benchmark's workload and launch configuration: 2400x1200 quads,
+    two-layer colouring, RCM + partition, block 480, AoS, FP64 data; the
+    oracle computes every cell."""
+    m, q, adt = case(2400, 1200)
+    if compute == "dw":
+        got = run_dw(ml, m, q, adt, "partition", "aos")
+    else:
+        got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64")
+    ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("variant", ["pipelined", "smem_atomic"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("reorder,block_size", [("partition", 480), ("rcm", 256), ("none", 480), ("partition", 1024)])
+def test_res_calc_staged_variants(ml, variant, dtype, reorder, block_size):
+    """The other staged implementations (pipelined persistent CTAs, shared-
+    memory atomics) against the oracle; unfit plans fall back to one block
+    per CTA."""
+    m, q, adt = case(97, 53)
+    ml.mp_set_staged_variant(variant)
+    try:
+        got, _ = run_res_calc(ml, m, q, adt, "hier", reorder, "aos", dtype, block_size=block_size)
+        ml.mp_check_device_status()
+    finally:
+        ml.mp_set_staged_variant("simple")
+    if dtype == "f64":
+        ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
+        assert rel_l2(got, ref) <= 1e-12
+    else:
+        ref = oracle.res_calc(m.edge2node, m.edge2cell, round_to(m.x, np.float32), round_to(q, np.float32),
+                              round_to(adt, np.float32))
+        assert rel_l2(got, ref) <= 1e-5

@@ -180,3 +180,51 @@ def test_map_renumber_roundtrip():
     inv = np.empty_like(pn)
     inv[pn] = np.arange(m.nnode)
     assert np.array_equal(out, inv[m.cell2node[pc]])
+
+
+def test_batch_fuses_plans():
+    """mesh_batch_build: one block table over the disjoint union of meshes;
+    the staged-kernel indexing invariant holds on the fused tables and
+    blocks are grouped by colour phase."""
+    meshes = [meshgen.quad_mesh(nx, ny, seed=s) for nx, ny, s in [(20, 10, 1), (33, 7, 2), (12, 12, 3)]]
+    opts = [(128, "partition"), (256, "rcm"), (64, "partition")]
+    plans = [ml.Plan(res_maps(m), m.nedge, block_size=bs, reorder=ro) for m, (bs, ro) in zip(meshes, opts)]
+    B = ml.Plan.batch(plans)
+    st = B.stats()
+    ne = sum(m.nedge for m in meshes)
+    nc = sum(m.ncell for m in meshes)
+    nn = sum(m.nnode for m in meshes)
+    assert st["from_size"] == ne and st["block_size"] == 256
+    assert st["nblocks"] == sum(p.stats()["nblocks"] for p in plans)
+    assert st["nblock_colors"] == max(p.stats()["nblock_colors"] for p in plans)
+    bo = B.table("block_offsets")
+    bc = B.table("block_color")
+    assert bo[0] == 0 and bo[-1] == ne and np.all(np.diff(bo) >= 1) and np.all(np.diff(bc) >= 0)
+    fp = B.table("footprint")
+    fs = B.table("fp_start").reshape(-1, 2)
+    fc = B.table("fp_count").reshape(-1, 2)
+    lm = B.table("local_map").reshape(ne, -1)
+    glob = np.concatenate([B.table("map", 0).reshape(-1, 2), B.table("map", 1).reshape(-1, 2)], axis=1)
+    for b in range(len(bo) - 1):
+        for it in range(bo[b], bo[b + 1]):
+            for k, s in enumerate([0, 0, 1, 1]):
+                assert fp[fs[b, s] + lm[it, k]] == glob[it, k]
+    # the fused maps are the per-mesh plan maps, offset into the concatenation
+    pe = B.perm(0)
+    assert PO.is_permutation(pe, ne) and PO.is_permutation(B.perm(2), nc) and PO.is_permutation(B.perm(1), nn)
+    offs_c = np.cumsum([0] + [m.ncell for m in meshes])
+    offs_n = np.cumsum([0] + [m.nnode for m in meshes])
+    offs_e = np.cumsum([0] + [m.nedge for m in meshes])
+    e2c_orig = np.concatenate([m.edge2cell + offs_c[i] for i, m in enumerate(meshes)])
+    inv_c = np.empty(nc, dtype=np.int64)
+    inv_c[B.perm(2)] = np.arange(nc)
+    assert np.array_equal(glob[:, 2:], inv_c[e2c_orig[pe]])
+    assert offs_e[-1] == ne and offs_n[-1] == nn
+    # same-colour blocks share no written cell
+    wr = PO.written_rows_of([{"to_set": 1, "idx": glob[:, :2], "to_size": nn, "written": False},
+                             {"to_set": 2, "idx": glob[:, 2:], "to_size": nc, "written": True}])
+    owner = {}
+    for b in range(len(bo) - 1):
+        for i in range(bo[b], bo[b + 1]):
+            for p in wr[i]:
+                assert owner.setdefault((bc[b], p), b) == b
