@@ -78,7 +78,8 @@ enum { MP_LAYOUT_AOS = 0, MP_LAYOUT_SOA = 1 };
 enum { MP_F64 = 0, MP_F32 = 1, MP_F64_DW = 2 };
 /* MP_F64_DW: FP64 data, arithmetic in double-word (pairs of FP32, ~48-bit
  * significand) on the FP32 pipes; results agree with FP64 to ~1e-13
- * relative.  Offered by loop_res_calc with HIER plans.                   */
+ * relative.  Offered by loop_res_calc and loop_elem_assemble with HIER
+ * plans (hex: blocks of at most 256 threads, thread-coloured increments). */
 
 /* One map of the loop: from the loop's iteration set (set id 0) to the
  * caller's set `to_set` (ids >= 1; maps with the same id share a to-set).
@@ -103,9 +104,14 @@ typedef struct {
     int32_t primary_map; /* map whose to-set is RCM-ordered; -1 = first written map  */
     int32_t data_reorder;/* 1: reorder to-set points by accessing blocks (Sec. 2.3.2);
                             -1: default (on with MP_REORDER_PARTITION)              */
+    int32_t staged;      /* MP_STAGED_* implementation of HIER loops; -1: the loop's
+                            default (MP_STAGED_SMEM_ATOMIC for hex assembly, whose 3D
+                            blocks need ~10 thread colours; MP_STAGED_SIMPLE otherwise) */
+    int32_t pad_;
 } mp_plan_opts;
 
-/* Fill opts with defaults: S = 512, PARTITION, HIER, AOS, l = 1.001. */
+/* Fill opts with defaults: S = 512, PARTITION, HIER, AOS, l = 1.001,
+ * staged = -1 (the loop's default). */
 void mp_plan_opts_default(mp_plan_opts *opts);
 
 typedef struct mp_plan mp_plan;
@@ -211,21 +217,21 @@ int mesh_plan_load(const char *path, mp_plan **out);
 int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                   void *res, double gam, double eps, void *stream);
 
-/* Implementations of the staged two-layer (HIER) loops (res_calc; hex
- * assembly follows SIMPLE or SMEM_ATOMIC, PIPELINED meaning SIMPLE there):
- *  MP_STAGED_SIMPLE (default): Algorithm 1 as printed, one block per CTA
- *    (with res prefetched at staging, so the write-back is a store);
- *  MP_STAGED_PIPELINED: persistent CTAs walk several blocks of a colour, and
- *    asynchronous copies (cp.async) stage block k+1's footprint while block
- *    k is computed (res_calc FP64/FP32, blocks of at most 512 threads whose
- *    two stages fit shared memory; other plans run SIMPLE);
- *  MP_STAGED_SMEM_ATOMIC: as SIMPLE, but the increments go to shared memory
- *    with atomic adds instead of one pass per thread colour (one barrier;
- *    the order of the additions, and so the rounding, is not fixed).
- * Block colouring still orders the write-back in every variant.
- * Process-wide setting; returns MP_EINVAL for an unknown value.           */
-enum { MP_STAGED_PIPELINED = 0, MP_STAGED_SIMPLE = 1, MP_STAGED_SMEM_ATOMIC = 2 };
-int mp_set_staged_variant(int32_t variant);
+/* Implementations of the staged two-layer (HIER) loops, chosen per plan
+ * with mp_plan_opts.staged:
+ *  MP_STAGED_SIMPLE: Algorithm 1 as printed, one block per CTA, increments
+ *    applied one thread colour at a time (res prefetched at staging, so the
+ *    write-back is a store);
+ *  MP_STAGED_PIPELINED: res_calc FP64/FP32 only: persistent CTAs walk
+ *    several blocks of a colour, and asynchronous copies (cp.async) stage
+ *    block k+1's footprint while block k is computed (blocks of at most 512
+ *    threads whose two stages fit shared memory; otherwise SIMPLE);
+ *  MP_STAGED_SMEM_ATOMIC: as SIMPLE, but increments go to shared memory with
+ *    atomic adds instead of one pass per thread colour (one barrier; the
+ *    order of additions, and so the rounding, is not fixed).  Not for the
+ *    double-word res_calc or the adjoint, which run SIMPLE.
+ * Block colouring orders the write-back in every variant.                */
+enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2 };
 
 /* Far-field boundary flux bres_calc over boundary edges: with
  * q_b = (q_c + qinf)/2,  res[c] += F(q_b).n + eps adt_c (q_c - qinf).

@@ -35,6 +35,7 @@ MP_MAX_BLOCK_COLORS = 256
 MP_MAX_MAPS = 4
 MP_MAX_TOSETS = 2
 REORDER = {"none": 0, "rcm": 1, "partition": 2}
+STAGED = {None: -1, "pipelined": 0, "simple": 1, "smem_atomic": 2}
 COLORING = {"hier": 0, "global": 1, "atomic": 2}
 LAYOUT = {"aos": 0, "soa": 1}
 DTYPE = {"f64": 0, "f32": 1, "f64dw": 2}
@@ -58,7 +59,8 @@ class mp_map(ctypes.Structure):
 class mp_plan_opts(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("reorder", ctypes.c_int32), ("coloring", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("imbalance", ctypes.c_double), ("eps", ctypes.c_double),
-                ("primary_map", ctypes.c_int32), ("data_reorder", ctypes.c_int32)]
+                ("primary_map", ctypes.c_int32), ("data_reorder", ctypes.c_int32), ("staged", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class mp_plan_stats(ctypes.Structure):
@@ -106,7 +108,6 @@ SIGNATURES = {
     "mp_error_string": (ctypes.c_char_p, [_I32]),
     "mp_check_device_status": (_I32, [_P]),
     "mp_version": (ctypes.c_char_p, []),
-    "mp_set_staged_variant": (_I32, [_I32]),
 }
 
 
@@ -147,7 +148,7 @@ class Plan:
 
     def __init__(self, maps, from_size: int, block_size: int = 512, reorder: str = "partition",
                  coloring: str = "hier", layout: str = "aos", imbalance: float = 1.001, eps: float = 0.0,
-                 primary_map: int = -1, data_reorder: int = -1, _handle=None):
+                 primary_map: int = -1, data_reorder: int = -1, staged: str | None = None, _handle=None):
         L = lib()
         self._h = ctypes.c_void_p()
         if _handle is not None:
@@ -173,6 +174,7 @@ class Plan:
         o.eps = float(eps)
         o.primary_map = int(primary_map)
         o.data_reorder = int(data_reorder)
+        o.staged = STAGED[staged]
         _check(L.mesh_plan_build(arr, n, int(from_size), ctypes.byref(o), ctypes.byref(self._h)),
                "mesh_plan_build")
         self.maps_meta = [(int(m["to_set"]), int(m["to_size"])) for m in maps]
@@ -340,8 +342,14 @@ def loop_update_noalloc(qold, q, res, adt, rms, layout: str = "aos", stream=None
                                      _ptr(rms), _stream(stream)), "loop_update_noalloc")
 
 
-def loop_elem_assemble(plan: Plan, x, v, sig, f, vol, kappa: float = 0.01, stream=None):
+def loop_elem_assemble(plan: Plan, x, v, sig, f, vol, kappa: float = 0.01, stream=None,
+                       compute: str | None = None):
+    """``compute="dw"`` selects double-word arithmetic on FP64 data (HIER plans)."""
     dt = _dtype_of(x, v, sig, f, vol)
+    if compute == "dw":
+        if dt != DTYPE["f64"]:
+            raise MeshLoopError(-1, "double-word arithmetic needs float64 data")
+        dt = DTYPE["f64dw"]
     _check(lib().loop_elem_assemble(plan.handle, dt, _ptr(x), _ptr(v), _ptr(sig), _ptr(f), _ptr(vol), kappa,
                                     _stream(stream)), "loop_elem_assemble")
 
@@ -351,14 +359,6 @@ def loop_adjoint(plan: Plan, x, q, adt, res_bar, q_bar, x_bar, gam: float = 1.4,
     dt = _dtype_of(x, q, adt, res_bar, q_bar, x_bar)
     _check(lib().loop_adjoint(plan.handle, dt, _ptr(x), _ptr(q), _ptr(adt), _ptr(res_bar), _ptr(q_bar),
                               _ptr(x_bar), gam, eps, _stream(stream)), "loop_adjoint")
-
-
-STAGED = {"pipelined": 0, "simple": 1, "smem_atomic": 2}
-
-
-def mp_set_staged_variant(variant: str):
-    """Select the staged two-layer implementation ("pipelined", "simple" or "smem_atomic")."""
-    _check(lib().mp_set_staged_variant(STAGED[variant]), "mp_set_staged_variant")
 
 
 def mp_check_device_status(stream=None):

@@ -49,12 +49,16 @@ int mp_plan_ensure_device(const mp_plan *plan);
 // Pipelined persistent two-layer res_calc (FP64 / FP32).
 int mp_res_calc_pipe(const mp_plan *P, int32_t dtype, const void *x, const void *q, const void *adt, void *res,
                      double gam, double eps, void *stream);
-// Current staged-kernel variant (mp_set_staged_variant).
-int mp_staged_variant();
+// Staged implementation of a HIER plan: opts.staged, or the loop default.
+inline int mp_staged(const mp_plan *P, int loop_default) { return P->opts.staged < 0 ? loop_default : P->opts.staged; }
 
 // Two-layer res_calc with FP64 data and double-word arithmetic.
 int mp_res_calc_dw(const mp_plan *P, const void *x, const void *q, const void *adt, void *res, double gam, double eps,
                    void *stream);
+
+// Two-layer hex assembly with FP64 data and double-word arithmetic.
+int mp_hex_dw(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, double kappa,
+              void *stream);
 
 // Library-owned device scratch for deterministic reductions (per device).
 int mp_reduce_scratch(double **partials, int *nparts);

@@ -287,19 +287,3 @@ extern "C" int loop_update_noalloc(int64_t ncell, int32_t dtype, int32_t layout,
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
-
-// ------------------------------------------------------ staged variant
-
-namespace {
-int g_staged_variant = MP_STAGED_SIMPLE;
-}
-
-extern "C" int mp_set_staged_variant(int32_t variant)
-{
-    if (variant != MP_STAGED_PIPELINED && variant != MP_STAGED_SIMPLE && variant != MP_STAGED_SMEM_ATOMIC)
-        return MP_EINVAL;
-    g_staged_variant = variant;
-    return MP_OK;
-}
-
-int mp_staged_variant() { return g_staged_variant; }

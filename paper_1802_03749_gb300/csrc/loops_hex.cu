@@ -270,7 +270,8 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
     if (P->opts.coloring == MP_COLOR_HIER) {
         const int cap = P->stats.footprint_max[0];
         const int smem = cap * hex_smem_per_node<T>();
-        auto kern = mp_staged_variant() == MP_STAGED_SMEM_ATOMIC ? hex_hier<T, SOA, true> : hex_hier<T, SOA, false>;
+        auto kern = mp_staged(P, MP_STAGED_SMEM_ATOMIC) == MP_STAGED_SMEM_ATOMIC ? hex_hier<T, SOA, true>
+                                                                                 : hex_hier<T, SOA, false>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
         int *err = nullptr;
@@ -302,13 +303,14 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
 extern "C" int loop_elem_assemble(const mp_plan *P, int32_t dtype, const void *x, const void *v, const void *sig,
                                   void *f, void *vol, double kappa, void *stream)
 {
-    if (!P || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
+    if (!P || (dtype != MP_F64 && dtype != MP_F32 && dtype != MP_F64_DW)) return MP_EINVAL;
     if (P->nmaps != 1 || P->maps[0].arity != 8 || !P->maps[0].written) return MP_EPLAN;
     if (P->from_size == 0) return MP_OK;
     for (const void *p : {x, v, sig, (const void *)f, (const void *)vol})
         if (!p || !aligned16(p)) return MP_EINVAL;
     int rc = mp_plan_ensure_device(P);
     if (rc != MP_OK) return rc;
+    if (dtype == MP_F64_DW) return mp_hex_dw(P, x, v, sig, f, vol, kappa, stream);
     cudaStream_t s = as_stream(stream);
     bool soa = P->opts.layout == MP_LAYOUT_SOA;
     if (dtype == MP_F64)

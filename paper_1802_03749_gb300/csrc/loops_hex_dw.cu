@@ -1,0 +1,246 @@
+// Hex assembly with FP64 data and double-word (FP32 pair) arithmetic: the
+// FP64-accurate variant for GB300, where about 550 FP64 operations per
+// element would otherwise run on the FP64 pipe (2 per clock per SM).
+//
+// Staged two-layer structure as hex_hier: the block's node footprint (x, v
+// converted to double-word, and the current f in FP64) is staged in shared
+// memory; each thread computes one element's forces in double-word
+// arithmetic; the 24 increments accumulate in double-word in shared memory
+// one thread colour at a time; each footprint node's f is written back once
+// (FP64 + double-word, two FP64 additions).  Element volumes are written
+// directly.  The formulas are those of the FP64 kernel (loops_hex.cu).
+#include "common.cuh"
+#include "dw.cuh"
+
+namespace {
+
+__device__ __forceinline__ constexpr int sx(int i) { return (i == 1 || i == 2 || i == 5 || i == 6) ? 1 : -1; }
+__device__ __forceinline__ constexpr int sy(int i) { return (i == 2 || i == 3 || i == 6 || i == 7) ? 1 : -1; }
+__device__ __forceinline__ constexpr int sz(int i) { return i >= 4 ? 1 : -1; }
+
+__device__ __forceinline__ dw ld2(const float2 *a, int i)
+{
+    float2 v = a[i];
+    return {v.x, v.y};
+}
+__device__ __forceinline__ void st2(float2 *a, int i, dw v) { a[i] = make_float2(v.hi, v.lo); }
+__device__ __forceinline__ dw sgn(dw x, int s) { return s > 0 ? x : dw_neg(x); }
+
+// a*b - c*d as one compensated sum
+__device__ __forceinline__ dw dw_det2(dw a, dw b, dw c, dw d)
+{
+    dw_acc A = dw_dot_begin(a, b);
+    dw_dot_add(A, dw_neg(c), d);
+    return dw_dot_end(A);
+}
+
+// smem per footprint node: x[3], v[3], increments[3] as double-word (72 B),
+// f[3] prefetched in FP64 (24 B), global id (4 B)
+constexpr int kHexDwNodeBytes = 9 * 8 + 24 + 4;
+
+template <bool SOA>
+__global__ void __launch_bounds__(256) hex_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
+                                                   const uint4 *__restrict__ lmap, const uint8_t *__restrict__ tcolor,
+                                                   const int32_t *__restrict__ fp, const double *__restrict__ x,
+                                                   const double *__restrict__ v, const double *__restrict__ sig,
+                                                   double *__restrict__ f, double *__restrict__ vol, int64_t nnode,
+                                                   int64_t nelem, int cap, dw kappa, int *__restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *s_f = reinterpret_cast<double *>(smem_raw);    // [3][cap] FP64
+    float2 *s_x = reinterpret_cast<float2 *>(s_f + 3 * cap);  // [3][cap]
+    float2 *s_v = s_x + 3 * cap;                           // [3][cap]
+    float2 *s_i = s_v + 3 * cap;                           // [3][cap] increments
+    int *s_gid = reinterpret_cast<int *>(s_i + 3 * cap);
+
+    const mp_block_desc d = desc[block0 + blockIdx.x];
+    const int tid = threadIdx.x;
+    const int nn = d.fp_count[0];
+    if ((unsigned)(reinterpret_cast<unsigned char *>(s_gid + cap) - smem_raw) > dynamic_smem_bytes() || nn > cap ||
+        d.nitems > (int)blockDim.x) {
+        if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
+        return;
+    }
+    const int32_t *fpn = fp + d.fp_start[0];
+    const bool active = tid < d.nitems;
+    uint4 l = make_uint4(0, 0, 0, 0);
+    int my_color = -1;
+    if (active) {
+        l = lmap[d.item_start + tid];
+        my_color = tcolor[d.item_start + tid];
+    }
+    for (int i = tid; i < nn; i += blockDim.x) {
+        const int64_t g = fpn[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t j = SOA ? a * nnode + g : 3 * g + a;
+            st2(s_x, a * cap + i, dw_from_double_int(x[j]));
+            st2(s_v, a * cap + i, dw_from_double_int(v[j]));
+            s_f[a * cap + i] = f[j];
+            s_i[a * cap + i] = make_float2(0.f, 0.f);
+        }
+        s_gid[i] = (int)g;
+    }
+    __syncthreads();
+    // Per element, with C = cof(J) and B_i = C xi_i:
+    //   stress   f_i[a] = -s_a B_i[a] = sum_b xi_i[b] t[a][b],  t[a][b] = -s_a C[a][b]
+    //   hourglass g_{k,i} = Gamma_{k,i} - (xi_i . w_k) / V,    w_k[b] = sum_a h_k[a] C[a][b]
+    //            q_k = kappa sum_j g_{k,j} v_j,  f_i -= sum_k g_{k,i} q_k
+    // so only t, w and q (not the 8 B_i) are kept between the two phases.
+    int loc[8];
+    dw t[3][3], w[4][3], qk[4][3], iV;
+    if (active) {
+        const int e = d.item_start + tid;
+        loc[0] = l.x & 0xffff;
+        loc[1] = l.x >> 16;
+        loc[2] = l.y & 0xffff;
+        loc[3] = l.y >> 16;
+        loc[4] = l.z & 0xffff;
+        loc[5] = l.z >> 16;
+        loc[6] = l.w & 0xffff;
+        loc[7] = l.w >> 16;
+        // J = 1/8 sum_i x_i xi_i^T
+        dw J[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const dw x0 = ld2(s_x, a * cap + loc[0]);
+            dw j0 = sgn(x0, sx(0)), j1 = sgn(x0, sy(0)), j2 = sgn(x0, sz(0));
+#pragma unroll
+            for (int i = 1; i < 8; ++i) {
+                const dw xi = ld2(s_x, a * cap + loc[i]);
+                j0 = dw_add_fast(j0, sgn(xi, sx(i)));
+                j1 = dw_add_fast(j1, sgn(xi, sy(i)));
+                j2 = dw_add_fast(j2, sgn(xi, sz(i)));
+            }
+            J[a][0] = dw_scale2(j0, 0.125f);
+            J[a][1] = dw_scale2(j1, 0.125f);
+            J[a][2] = dw_scale2(j2, 0.125f);
+        }
+        dw C[3][3];
+        C[0][0] = dw_det2(J[1][1], J[2][2], J[1][2], J[2][1]);
+        C[0][1] = dw_det2(J[1][2], J[2][0], J[1][0], J[2][2]);
+        C[0][2] = dw_det2(J[1][0], J[2][1], J[1][1], J[2][0]);
+        C[1][0] = dw_det2(J[0][2], J[2][1], J[0][1], J[2][2]);
+        C[1][1] = dw_det2(J[0][0], J[2][2], J[0][2], J[2][0]);
+        C[1][2] = dw_det2(J[0][1], J[2][0], J[0][0], J[2][1]);
+        C[2][0] = dw_det2(J[0][1], J[1][2], J[0][2], J[1][1]);
+        C[2][1] = dw_det2(J[0][2], J[1][0], J[0][0], J[1][2]);
+        C[2][2] = dw_det2(J[0][0], J[1][1], J[0][1], J[1][0]);
+        dw_acc A = dw_dot_begin(J[0][0], C[0][0]);
+        dw_dot_add(A, J[0][1], C[0][1]);
+        dw_dot_add(A, J[0][2], C[0][2]);
+        const dw V = dw_scale2(dw_dot_end(A), 8.0f);
+        vol[e] = dw_to_double(V);
+        iV = dw_recip(V);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const dw sa = dw_from_double_int(SOA ? sig[a * nelem + e] : sig[3 * (int64_t)e + a]);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) t[a][b] = dw_neg(dw_mul(sa, C[a][b]));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int G[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                G[j] = k == 0 ? sy(j) * sz(j) : (k == 1 ? sx(j) * sz(j) : (k == 2 ? sx(j) * sy(j) : sx(j) * sy(j) * sz(j)));
+            dw h[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                h[a] = sgn(ld2(s_x, a * cap + loc[0]), G[0]);
+#pragma unroll
+                for (int j = 1; j < 8; ++j) h[a] = dw_add_fast(h[a], sgn(ld2(s_x, a * cap + loc[j]), G[j]));
+            }
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                dw_acc P = dw_dot_begin(h[0], C[0][b]);
+                dw_dot_add(P, h[1], C[1][b]);
+                dw_dot_add(P, h[2], C[2][b]);
+                w[k][b] = dw_dot_end(P);
+            }
+            dw_acc Q[3];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const dw xb = dw_add_fast(dw_add_fast(sgn(w[k][0], sx(j)), sgn(w[k][1], sy(j))), sgn(w[k][2], sz(j)));
+                const dw gj = dw_add_fast(dw{(float)G[j], 0.f}, dw_neg(dw_mul(xb, iV)));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const dw vj = ld2(s_v, a * cap + loc[j]);
+                    if (j == 0)
+                        Q[a] = dw_dot_begin(gj, vj);
+                    else
+                        dw_dot_add(Q[a], gj, vj);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) qk[k][a] = dw_mul(dw_dot_end(Q[a]), kappa);
+        }
+    }
+    for (int c = 0; c < d.ncolors; ++c) {
+        if (my_color == c) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                dw gi[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int Gk = k == 0 ? sy(i) * sz(i)
+                                          : (k == 1 ? sx(i) * sz(i) : (k == 2 ? sx(i) * sy(i) : sx(i) * sy(i) * sz(i)));
+                    const dw xb = dw_add_fast(dw_add_fast(sgn(w[k][0], sx(i)), sgn(w[k][1], sy(i))), sgn(w[k][2], sz(i)));
+                    gi[k] = dw_add_fast(dw{(float)Gk, 0.f}, dw_neg(dw_mul(xb, iV)));
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    dw fa = dw_add_fast(dw_add_fast(sgn(t[a][0], sx(i)), sgn(t[a][1], sy(i))), sgn(t[a][2], sz(i)));
+                    dw_acc H = dw_dot_begin(gi[0], qk[0][a]);
+                    dw_dot_add(H, gi[1], qk[1][a]);
+                    dw_dot_add(H, gi[2], qk[2][a]);
+                    dw_dot_add(H, gi[3], qk[3][a]);
+                    fa = dw_add_fast(fa, dw_neg(dw_dot_end(H)));
+                    st2(s_i, a * cap + loc[i], dw_add_fast(ld2(s_i, a * cap + loc[i]), fa));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < nn; i += blockDim.x) {
+        const int64_t g = s_gid[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[SOA ? a * nnode + g : 3 * g + a] = f64_add_dw(s_f[a * cap + i], ld2(s_i, a * cap + i));
+    }
+}
+
+template <bool SOA>
+int hex_dw_t(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, double kappa,
+             cudaStream_t s)
+{
+    if (P->opts.block_size > 256) return MP_EINVAL;
+    const int cap = P->stats.footprint_max[0];
+    const int smem = cap * kHexDwNodeBytes;
+    auto kern = hex_hier_dw<SOA>;
+    int rc = mp_allow_smem(kern, smem);
+    if (rc != MP_OK) return rc;
+    int *err = nullptr;
+    if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
+    const float kh = (float)kappa;
+    const dw kap{kh, (float)(kappa - (double)kh)};
+    for (int c = 0; c < P->ncolors; ++c) {
+        const int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
+        if (nb == 0) continue;
+        kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const uint4 *>(P->dev.lmap),
+                                                  P->dev.tcolor, P->dev.fp, (const double *)x, (const double *)v,
+                                                  (const double *)sig, (double *)f, (double *)vol,
+                                                  P->maps[0].to_size, P->from_size, cap, kap, err);
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+}  // namespace
+
+int mp_hex_dw(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, double kappa,
+              void *stream)
+{
+    if (P->opts.coloring != MP_COLOR_HIER) return MP_EPLAN;
+    return P->opts.layout == MP_LAYOUT_SOA ? hex_dw_t<true>(P, x, v, sig, f, vol, kappa, as_stream(stream))
+                                           : hex_dw_t<false>(P, x, v, sig, f, vol, kappa, as_stream(stream));
+}

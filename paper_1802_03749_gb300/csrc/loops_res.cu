@@ -400,8 +400,8 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         if (P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
         const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
         const int smem = cap_c * res_smem_per_cell<T>() + cap_n * res_smem_per_node<T>();
-        auto kern = mp_staged_variant() == MP_STAGED_SMEM_ATOMIC ? res_calc_hier<T, SOA, true>
-                                                                 : res_calc_hier<T, SOA, false>;
+        auto kern = mp_staged(P, MP_STAGED_SIMPLE) == MP_STAGED_SMEM_ATOMIC ? res_calc_hier<T, SOA, true>
+                                                                            : res_calc_hier<T, SOA, false>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
         int *err = nullptr;
@@ -478,7 +478,7 @@ extern "C" int loop_res_calc(const mp_plan *P, int32_t dtype, const void *x, con
     int rc = mp_plan_ensure_device(P);
     if (rc != MP_OK) return rc;
     if (dtype == MP_F64_DW) return mp_res_calc_dw(P, x, q, adt, res, gam, eps, stream);
-    if (P->opts.coloring == MP_COLOR_HIER && mp_staged_variant() == MP_STAGED_PIPELINED) {
+    if (P->opts.coloring == MP_COLOR_HIER && mp_staged(P, MP_STAGED_SIMPLE) == MP_STAGED_PIPELINED) {
         rc = mp_res_calc_pipe(P, dtype, x, q, adt, res, gam, eps, stream);
         if (rc != MP_EPLAN) return rc;  // otherwise the layout does not fit: one block per CTA
     }

@@ -24,7 +24,7 @@ namespace {
 // Dynamic shared memory for cap_c cells and cap_n nodes:
 //   double x, y                                    (16 B per node)
 //   double res[4]  (prefetched at staging)         (32 B per cell)
-//   dw   rho, ru, rv, E, adt, u, v, p, H, inc[4]   (13 x 8 B per cell)
+//   dw   rho, ru, rv, E, eps adt/2, u, v, p, H, inc[4]   (13 x 8 B per cell)
 //   int  gid                                       (4 B per cell)
 // The FP64 arrays come first (8-byte alignment).
 constexpr int kDwCellBytes = 32 + 13 * 8 + 4;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(512, 2) res_calc_hier_dw(const mp_block_desc *
         st(s_ru, i, RU);
         st(s_rv, i, RV);
         st(s_E, i, EE);
-        st(s_a, i, dw_from_double_int(adt[g]));
+        st(s_a, i, dw_mul(dw_from_double_int(adt[g]), half_eps));  // eps adt / 2
         st(s_u, i, u);
         st(s_v, i, v);
         st(s_p, i, p);
@@ -149,15 +149,43 @@ __global__ void __launch_bounds__(512, 2) res_calc_hier_dw(const mp_block_desc *
         const dw r1 = ld(s_r, c1), r2 = ld(s_r, c2);
         const dw ru1 = ld(s_ru, c1), ru2 = ld(s_ru, c2);
         const dw rv1 = ld(s_rv, c1), rv2 = ld(s_rv, c2);
-        const dw V1 = dw_add_fast(dw_mul(ld(s_u, c1), nxh), dw_mul(ld(s_v, c1), nyh));
-        const dw V2 = dw_add_fast(dw_mul(ld(s_u, c2), nxh), dw_mul(ld(s_v, c2), nyh));
-        const dw ps = dw_add_fast(ld(s_p, c1), ld(s_p, c2));
-        const dw mu = dw_mul(dw_add_fast(ld(s_a, c1), ld(s_a, c2)), half_eps);
-        f[0] = dw_add_fast(dw_add_fast(dw_mul(r1, V1), dw_mul(r2, V2)), dw_mul(mu, dw_add_fast(r1, dw_neg(r2))));
-        f[1] = dw_add_fast(dw_add_fast(dw_add_fast(dw_mul(ru1, V1), dw_mul(ru2, V2)), dw_mul(ps, nxh)), dw_mul(mu, dw_add_fast(ru1, dw_neg(ru2))));
-        f[2] = dw_add_fast(dw_add_fast(dw_add_fast(dw_mul(rv1, V1), dw_mul(rv2, V2)), dw_mul(ps, nyh)), dw_mul(mu, dw_add_fast(rv1, dw_neg(rv2))));
-        f[3] = dw_add_fast(dw_add_fast(dw_mul(ld(s_H, c1), V1), dw_mul(ld(s_H, c2), V2)),
-                      dw_mul(mu, dw_add_fast(ld(s_E, c1), dw_neg(ld(s_E, c2)))));
+        const dw p1 = ld(s_p, c1), p2 = ld(s_p, c2);
+        // each component is one compensated sum of products:
+        //   V = u nx/2 + v ny/2,  mu = eps (adt1 + adt2) / 2,
+        //   f0 = r1 V1 + r2 V2 + mu r1 - mu r2
+        //   f1 = ru1 V1 + ru2 V2 + p1 nx/2 + p2 nx/2 + mu ru1 - mu ru2   (f2 likewise)
+        //   f3 = H1 V1 + H2 V2 + mu E1 - mu E2
+        dw_acc A = dw_dot_begin(ld(s_u, c1), nxh);
+        dw_dot_add(A, ld(s_v, c1), nyh);
+        const dw V1 = dw_dot_end(A);
+        A = dw_dot_begin(ld(s_u, c2), nxh);
+        dw_dot_add(A, ld(s_v, c2), nyh);
+        const dw V2 = dw_dot_end(A);
+        const dw mu = dw_add_fast(ld(s_a, c1), ld(s_a, c2));
+        A = dw_dot_begin(r1, V1);
+        dw_dot_add(A, r2, V2);
+        dw_dot_add(A, mu, r1);
+        dw_dot_add(A, mu, dw_neg(r2));
+        f[0] = dw_dot_end(A);
+        A = dw_dot_begin(ru1, V1);
+        dw_dot_add(A, ru2, V2);
+        dw_dot_add(A, p1, nxh);
+        dw_dot_add(A, p2, nxh);
+        dw_dot_add(A, mu, ru1);
+        dw_dot_add(A, mu, dw_neg(ru2));
+        f[1] = dw_dot_end(A);
+        A = dw_dot_begin(rv1, V1);
+        dw_dot_add(A, rv2, V2);
+        dw_dot_add(A, p1, nyh);
+        dw_dot_add(A, p2, nyh);
+        dw_dot_add(A, mu, rv1);
+        dw_dot_add(A, mu, dw_neg(rv2));
+        f[2] = dw_dot_end(A);
+        A = dw_dot_begin(ld(s_H, c1), V1);
+        dw_dot_add(A, ld(s_H, c2), V2);
+        dw_dot_add(A, mu, ld(s_E, c1));
+        dw_dot_add(A, mu, dw_neg(ld(s_E, c2)));
+        f[3] = dw_dot_end(A);
     }
     for (int c = 0; c < d.ncolors; ++c) {
         if (my_color == c) {

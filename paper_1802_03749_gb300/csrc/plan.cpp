@@ -664,6 +664,7 @@ int build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_op
     if (o.reorder < 0 || o.reorder > 2 || o.coloring < 0 || o.coloring > 2 || o.layout < 0 || o.layout > 1)
         return MP_EINVAL;
     if (!(o.imbalance >= 1.0) || o.imbalance > 2.0) return MP_EINVAL;
+    if (o.staged < -1 || o.staged > 2) return MP_EINVAL;
     if (o.data_reorder < 0) o.data_reorder = (o.reorder == MP_REORDER_PARTITION) ? 1 : 0;
     P->opts = o;
     P->from_size = from_size;
@@ -824,6 +825,8 @@ void mp_plan_opts_default(mp_plan_opts *o)
     o->eps = 0.0;
     o->primary_map = -1;
     o->data_reorder = -1;
+    o->staged = -1;
+    o->pad_ = 0;
 }
 
 int mesh_plan_build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_opts *opts, mp_plan **out)

@@ -21,10 +21,11 @@ def case(n):
     return CASES[n]
 
 
-def run_hex(m, sig, v, coloring, reorder, layout, dtype, block_size=256):
+def run_hex(m, sig, v, coloring, reorder, layout, dtype, block_size=256, staged=None):
     import paper_1802_03749_gb300 as ml
     from paper_1802_03749_gb300.mesh import HexPlan
-    H = HexPlan(m.nnode, m.elem2node, block_size=block_size, reorder=reorder, coloring=coloring, layout=layout)
+    H = HexPlan(m.nnode, m.elem2node, block_size=block_size, reorder=reorder, coloring=coloring, layout=layout,
+                staged=staged)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     x = torch.tensor(H.to_plan(m.x, "node"), dtype=tdt, device="cuda")
     vd = torch.tensor(H.to_plan(v, "node"), dtype=tdt, device="cuda")
@@ -66,14 +67,11 @@ def test_hex_block_sizes_ragged(block_size):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_hex_smem_atomic_variant(dtype):
-    import paper_1802_03749_gb300 as ml
+def test_hex_thread_coloured_variant(dtype):
+    """Hex assembly defaults to shared-memory atomics; the thread-coloured
+    increments of Algorithm 1 are the other staged variant."""
     m, sig, v = case(14)
-    ml.mp_set_staged_variant("smem_atomic")
-    try:
-        f, vol, _ = run_hex(m, sig, v, "hier", "partition", "aos", dtype)
-    finally:
-        ml.mp_set_staged_variant("simple")
+    f, vol, _ = run_hex(m, sig, v, "hier", "partition", "aos", dtype, staged="simple")
     if dtype == "f64":
         fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
         assert rel_l2(f, fr) <= 1e-12
@@ -81,3 +79,41 @@ def test_hex_smem_atomic_variant(dtype):
         fr, vr = oracle.hex_force(m.elem2node, round_to(m.x, np.float32), round_to(v, np.float32),
                                   round_to(sig, np.float32))
         assert rel_l2(f, fr) <= 1e-5
+
+
+def run_hex_dw(m, sig, v, reorder, layout, block_size=128):
+    import paper_1802_03749_gb300 as ml
+    from paper_1802_03749_gb300.mesh import HexPlan
+    H = HexPlan(m.nnode, m.elem2node, block_size=block_size, reorder=reorder, coloring="hier", layout=layout)
+    x = torch.tensor(H.to_plan(m.x, "node"), device="cuda")
+    vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
+    sd = torch.tensor(H.to_plan(sig, "elem"), device="cuda")
+    f0 = np.cos(np.arange(m.nnode * 3)).reshape(-1, 3)          # increments are "+="
+    f = torch.tensor(H.to_plan(f0, "node"), device="cuda")
+    vol = torch.zeros(m.nelem, dtype=torch.float64, device="cuda")
+    ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01, compute="dw")
+    ml.mp_check_device_status()
+    return (H.from_plan(f.cpu().numpy(), "node", 3) - f0, H.from_plan(vol.cpu().numpy(), "elem", 1))
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("reorder", ["partition", "rcm"])
+def test_hex_double_word_parity(reorder, layout):
+    """FP64 data with double-word arithmetic: within the FP64 bar."""
+    m, sig, v = case(14)
+    f, vol = run_hex_dw(m, sig, v, reorder, layout)
+    fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
+    assert rel_l2(vol, vr) <= 1e-12
+    assert rel_l2(f, fr) <= 1e-12
+
+
+@pytest.mark.slow
+def test_hex_double_word_full_size():
+    """The benchmark's hex workload, 120^3 elements: the oracle computes
+    every node."""
+    m = meshgen.hex_mesh(120)
+    sig, v = meshgen.hex_fields(m)
+    f, vol = run_hex_dw(m, sig, v, "partition", "aos")
+    fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
+    assert rel_l2(vol, vr) <= 1e-12
+    assert rel_l2(f, fr) <= 1e-12

@@ -29,10 +29,10 @@ def case(nx, ny):
     return CASES[(nx, ny)]
 
 
-def run_res_calc(ml, m, q, adt, coloring, reorder, layout, dtype, block_size=480, res0=None):
+def run_res_calc(ml, m, q, adt, coloring, reorder, layout, dtype, block_size=480, res0=None, staged=None):
     from paper_1802_03749_gb300.mesh import AirfoilPlans
     P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                     block_size=block_size, reorder=reorder, coloring=coloring, layout=layout)
+                     block_size=block_size, reorder=reorder, coloring=coloring, layout=layout, staged=staged)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     dev = "cuda"
     x = torch.tensor(P.to_plan(m.x, "node"), dtype=tdt, device=dev)
@@ -144,12 +144,8 @@ def test_res_calc_staged_variants(ml, variant, dtype, reorder, block_size):
     memory atomics) against the oracle; unfit plans fall back to one block
     per CTA."""
     m, q, adt = case(97, 53)
-    ml.mp_set_staged_variant(variant)
-    try:
-        got, _ = run_res_calc(ml, m, q, adt, "hier", reorder, "aos", dtype, block_size=block_size)
-        ml.mp_check_device_status()
-    finally:
-        ml.mp_set_staged_variant("simple")
+    got, _ = run_res_calc(ml, m, q, adt, "hier", reorder, "aos", dtype, block_size=block_size, staged=variant)
+    ml.mp_check_device_status()
     if dtype == "f64":
         ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
         assert rel_l2(got, ref) <= 1e-12
