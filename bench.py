@@ -236,9 +236,20 @@ class Timer:
 
 def bench_rows(ml, torch, timer, args):
     """Measurements of the other loops (not the headline): hex assembly,
-    the adjoint and the batched graph-captured time step."""
-    from paper_1802_03749_gb300 import autotune
-    from paper_1802_03749_gb300.mesh import AirfoilBatch, AirfoilPlans, AirfoilStep, HexPlan
+    the adjoint and the batched graph-captured time step (``--rows``)."""
+    rows = {}
+    want = set(args.rows.split(",")) if args.rows else set()
+    if "hex" in want:
+        rows.update(bench_hex(ml, torch, timer, args))
+    if "adjoint" in want:
+        rows.update(bench_adjoint(ml, torch, timer, args))
+    if "batch" in want:
+        rows.update(bench_batch(ml, torch, timer, args))
+    return rows
+
+
+def bench_hex(ml, torch, timer, args):
+    from paper_1802_03749_gb300.mesh import HexPlan
     hbm, _ = read_peaks()
     rows = {}
     # hex assembly, n^3 elements
@@ -265,23 +276,53 @@ def bench_rows(ml, torch, timer, args):
                 "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
                 "reuse": st["reuse_all"]}
             del x, vd, sd, f, vol
+    # hex assembly with FP64 data in double-word arithmetic (two-layer, S = 128)
+    H = HexPlan(hm.nnode, hm.elem2node, block_size=128, reorder="rcm", coloring="hier")
+    H.plan.upload()
+    x = torch.tensor(H.to_plan(hm.x, "node"), device="cuda")
+    vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
+    sd = torch.tensor(H.to_plan(sig, "elem"), device="cuda")
+    f = torch.zeros_like(x)
+    vol = torch.zeros(hm.nelem, dtype=torch.float64, device="cuda")
+    ms, _ = timer(lambda: ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01, compute="dw"), 10, 2)
+    ub = useful_bytes_hex(hm.nelem, hm.nnode, 8)
+    st = H.plan.stats()
+    rows["hex_f64dw_hier_rcm"] = {
+        "workload": f"hex assembly {args.hex_n}^3 elements, double-word arithmetic", "ms": ms,
+        "gelems_s": hm.nelem / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
+        "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"], "reuse": st["reuse_all"]}
+    del x, vd, sd, f, vol
+    return rows
+
+
+def bench_adjoint(ml, torch, timer, args):
+    from paper_1802_03749_gb300.mesh import AirfoilPlans
+    hbm, _ = read_peaks()
+    rows = {}
     # adjoint, 1200x600
     am = meshgen.quad_mesh(1200, 600)
     aq = meshgen.quad_state(am.ncell)
     aadt = synthetic_adt(am)
     rb = meshgen.adjoint_seed(am.ncell)
-    for coloring, reorder in (("hier", "partition"), ("atomic", "rcm")):
+    for coloring, reorder, comp in (("hier", "partition", None), ("hier", "partition", "dw"), ("atomic", "rcm", None)):
         P = AirfoilPlans(am.ncell, am.nnode, am.edge2node, am.edge2cell, am.bedge2node, am.bedge2cell, am.cell2node,
-                         block_size=384, reorder=reorder, coloring=coloring, adjoint=True)
+                         block_size=256 if comp else 384, reorder=reorder, coloring=coloring, adjoint=True)
         P.res.upload()
         t = lambda a, w: torch.tensor(P.to_plan(a, w), device="cuda")
         x, qd, ad, rbd = t(am.x, "node"), t(aq, "cell"), t(aadt, "cell"), t(rb, "cell")
         qb, xb = torch.zeros_like(qd), torch.zeros_like(x)
-        ms, _ = timer(lambda: ml.loop_adjoint(P.res, x, qd, ad, rbd, qb, xb), 10, 2)
+        ms, _ = timer(lambda: ml.loop_adjoint(P.res, x, qd, ad, rbd, qb, xb, compute=comp), 10, 2)
         ub = useful_bytes_adjoint(am.ncell, am.nnode, am.nedge)
-        rows[f"adjoint_f64_{coloring}_{reorder}"] = {
+        rows[f"adjoint_{'f64dw' if comp else 'f64'}_{coloring}_{reorder}"] = {
             "workload": "res_calc adjoint 1200x600", "ms": ms, "gedges_s": am.nedge / ms / 1e6,
             "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm}
+    return rows
+
+
+def bench_batch(ml, torch, timer, args):
+    from paper_1802_03749_gb300 import autotune
+    from paper_1802_03749_gb300.mesh import AirfoilBatch, AirfoilPlans, AirfoilStep
+    rows = {}
     # batched time step: meshes of uneven size, FP32 data, FP64 update and sum
     sizes = meshgen.batch_sizes(args.batch)
     meshes = [meshgen.quad_mesh(nx, ny, seed=meshgen.DEFAULT_SEED + 97 * i) for i, (nx, ny) in enumerate(sizes)]
@@ -321,11 +362,13 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--block-size", type=int, default=128)
+    ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--layout", default="aos", choices=["aos", "soa"])
     ap.add_argument("--compute", default="dw", choices=["dw", "f64", "f32"],
                     help="dw: FP64 data with double-word arithmetic; f64: native FP64; f32: FP32 data")
     ap.add_argument("--no-variants", action="store_true", help="skip the baseline variants")
+    ap.add_argument("--rows", default="hex,adjoint,batch",
+                    help="other loops to measure (comma list of hex, adjoint, batch; empty for none)")
     ap.add_argument("--no-rows", action="store_true", help="skip the hex / adjoint / batch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--nx", type=int, default=NX, help="quad grid size (profiling runs use smaller meshes)")

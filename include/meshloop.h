@@ -78,8 +78,9 @@ enum { MP_LAYOUT_AOS = 0, MP_LAYOUT_SOA = 1 };
 enum { MP_F64 = 0, MP_F32 = 1, MP_F64_DW = 2 };
 /* MP_F64_DW: FP64 data, arithmetic in double-word (pairs of FP32, ~48-bit
  * significand) on the FP32 pipes; results agree with FP64 to ~1e-13
- * relative.  Offered by loop_res_calc and loop_elem_assemble with HIER
- * plans (hex: blocks of at most 256 threads, thread-coloured increments). */
+ * relative.  Offered by loop_res_calc, loop_adjoint and loop_elem_assemble
+ * with HIER plans (thread-coloured increments; hex: blocks of at most 256
+ * threads).                                                              */
 
 /* One map of the loop: from the loop's iteration set (set id 0) to the
  * caller's set `to_set` (ids >= 1; maps with the same id share a to-set).
@@ -298,7 +299,7 @@ int loop_elem_assemble(const mp_plan *plan, int32_t dtype, const void *x, const 
 /* Adjoint of res_calc with x, q, adt fixed (adt not differentiated):
  *   q_bar += (d res/d q)^T res_bar,  x_bar += (d res/d x)^T res_bar.
  * Both maps are written, so the plan has maps {edge->node (2, written),
- * edge->cell (2, written)}.  FP64 only.                                  */
+ * edge->cell (2, written)}.  dtype MP_F64, MP_F32 or MP_F64_DW.         */
 int loop_adjoint(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                  const void *res_bar, void *q_bar, void *x_bar, double gam, double eps,
                  void *stream);

@@ -355,8 +355,13 @@ def loop_elem_assemble(plan: Plan, x, v, sig, f, vol, kappa: float = 0.01, strea
 
 
 def loop_adjoint(plan: Plan, x, q, adt, res_bar, q_bar, x_bar, gam: float = 1.4, eps: float = 0.05,
-                 stream=None):
+                 stream=None, compute: str | None = None):
+    """``compute="dw"`` selects double-word arithmetic on FP64 data (HIER plans)."""
     dt = _dtype_of(x, q, adt, res_bar, q_bar, x_bar)
+    if compute == "dw":
+        if dt != DTYPE["f64"]:
+            raise MeshLoopError(-1, "double-word arithmetic needs float64 data")
+        dt = DTYPE["f64dw"]
     _check(lib().loop_adjoint(plan.handle, dt, _ptr(x), _ptr(q), _ptr(adt), _ptr(res_bar), _ptr(q_bar),
                               _ptr(x_bar), gam, eps, _stream(stream)), "loop_adjoint")
 

@@ -60,6 +60,10 @@ int mp_res_calc_dw(const mp_plan *P, const void *x, const void *q, const void *a
 int mp_hex_dw(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, double kappa,
               void *stream);
 
+// Two-layer res_calc adjoint with FP64 data and double-word arithmetic.
+int mp_adjoint_dw(const mp_plan *P, const void *x, const void *q, const void *adt, const void *rbar, void *qbar,
+                  void *xbar, double gam, double eps, void *stream);
+
 // Library-owned device scratch for deterministic reductions (per device).
 int mp_reduce_scratch(double **partials, int *nparts);
 

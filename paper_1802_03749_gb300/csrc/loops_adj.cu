@@ -293,7 +293,7 @@ int adjoint_t(const mp_plan *P, const void *x, const void *q, const void *adt, c
 extern "C" int loop_adjoint(const mp_plan *P, int32_t dtype, const void *x, const void *q, const void *adt,
                             const void *res_bar, void *q_bar, void *x_bar, double gam, double eps, void *stream)
 {
-    if (!P || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
+    if (!P || (dtype != MP_F64 && dtype != MP_F32 && dtype != MP_F64_DW)) return MP_EINVAL;
     if (P->nmaps != 2 || P->maps[0].arity != 2 || P->maps[1].arity != 2 || !P->maps[0].written ||
         !P->maps[1].written)
         return MP_EPLAN;
@@ -302,6 +302,7 @@ extern "C" int loop_adjoint(const mp_plan *P, int32_t dtype, const void *x, cons
         if (!p || !aligned16(p)) return MP_EINVAL;
     int rc = mp_plan_ensure_device(P);
     if (rc != MP_OK) return rc;
+    if (dtype == MP_F64_DW) return mp_adjoint_dw(P, x, q, adt, res_bar, q_bar, x_bar, gam, eps, stream);
     cudaStream_t s = as_stream(stream);
     bool soa = P->opts.layout == MP_LAYOUT_SOA;
     if (dtype == MP_F64)

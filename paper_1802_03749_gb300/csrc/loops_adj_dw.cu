@@ -1,0 +1,255 @@
+// Adjoint of res_calc with FP64 data and double-word (FP32 pair)
+// arithmetic, the FP64-accurate variant for GB300 (see loops_res_dw.cu).
+// Same staged two-layer structure and formulas as adjoint_hier
+// (loops_adj.cu): per edge, with f_bar = res_bar[c1] - res_bar[c2] and
+// h = f_bar / 2, each side's reverse sweep of F(q).n is
+//   V = u . n,  Vb = h0 rho + h1 rho u + h2 rho v + h3 H,
+//   pb = h1 n_x + h2 n_y + h3 V,  Wb = Vb / rho,  gpb = (gam-1) pb,
+//   q_b = (h0 V - Wb V + gpb |u|^2/2,  h1 V + Wb n_x - gpb u,
+//          h2 V + Wb n_y - gpb v,  h3 V + gpb),
+//   n_b += (h1 p + Wb rho u,  h2 p + Wb rho v),
+// plus mu f_bar on q1 and -mu f_bar on q2; each component is one
+// compensated sum of products.  The edge normal is formed in FP64.
+#include "common.cuh"
+#include "dw.cuh"
+
+namespace {
+
+__device__ __forceinline__ dw ldw(const float2 *a, int i)
+{
+    float2 v = a[i];
+    return {v.x, v.y};
+}
+__device__ __forceinline__ void stw(float2 *a, int i, dw v) { a[i] = make_float2(v.hi, v.lo); }
+
+// Dynamic shared memory for cap_c cells and cap_n nodes:
+//   double x, y, xbar[2]                  (32 B per node)
+//   double qbar[4]                        (32 B per cell)
+//   dw rho, ru, rv, H, ri, u, v, p, K, a' (10 x 8 B per cell; K = |u|^2/2,
+//                                          a' = eps adt / 2)
+//   dw rb[4], qinc[4]                     (64 B per cell)
+//   dw xinc[2]                            (16 B per node)
+//   int gid per cell and node
+constexpr int kAdjDwCellBytes = 32 + 80 + 64 + 4;
+constexpr int kAdjDwNodeBytes = 32 + 16 + 4;
+
+// One side's reverse sweep; accumulates n_b.
+__device__ __forceinline__ void flux_rev_dw(const float2 *const S[10], int c, dw nx, dw ny, const dw h[4], dw gm1,
+                                            dw qb[4], dw_acc &nbx, dw_acc &nby, bool first)
+{
+    const dw r = ldw(S[0], c), ru = ldw(S[1], c), rv = ldw(S[2], c), H = ldw(S[3], c), ri = ldw(S[4], c);
+    const dw u = ldw(S[5], c), v = ldw(S[6], c), p = ldw(S[7], c), K = ldw(S[8], c);
+    dw_acc A = dw_dot_begin(u, nx);
+    dw_dot_add(A, v, ny);
+    const dw V = dw_dot_end(A);
+    A = dw_dot_begin(h[0], r);
+    dw_dot_add(A, h[1], ru);
+    dw_dot_add(A, h[2], rv);
+    dw_dot_add(A, h[3], H);
+    const dw Wb = dw_mul(dw_dot_end(A), ri);
+    A = dw_dot_begin(h[1], nx);
+    dw_dot_add(A, h[2], ny);
+    dw_dot_add(A, h[3], V);
+    const dw gpb = dw_mul(gm1, dw_dot_end(A));
+    A = dw_dot_begin(h[0], V);
+    dw_dot_add(A, dw_neg(Wb), V);
+    dw_dot_add(A, gpb, K);
+    qb[0] = dw_dot_end(A);
+    A = dw_dot_begin(h[1], V);
+    dw_dot_add(A, Wb, nx);
+    dw_dot_add(A, dw_neg(gpb), u);
+    qb[1] = dw_dot_end(A);
+    A = dw_dot_begin(h[2], V);
+    dw_dot_add(A, Wb, ny);
+    dw_dot_add(A, dw_neg(gpb), v);
+    qb[2] = dw_dot_end(A);
+    qb[3] = dw_add_fast(dw_mul(h[3], V), gpb);
+    if (first) {
+        nbx = dw_dot_begin(h[1], p);
+        nby = dw_dot_begin(h[2], p);
+    } else {
+        dw_dot_add(nbx, h[1], p);
+        dw_dot_add(nby, h[2], p);
+    }
+    dw_dot_add(nbx, Wb, ru);
+    dw_dot_add(nby, Wb, rv);
+}
+
+template <bool SOA>
+__global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
+                                                          const ushort4 *__restrict__ lmap,
+                                                          const uint8_t *__restrict__ tcolor,
+                                                          const int32_t *__restrict__ fp, const double *__restrict__ x,
+                                                          const double *__restrict__ q,
+                                                          const double *__restrict__ adt,
+                                                          const double *__restrict__ rbar, double *__restrict__ qbar,
+                                                          double *__restrict__ xbar, int64_t nnode, int64_t ncell,
+                                                          int cap_c, int cap_n, dw gm1, dw half_eps,
+                                                          int *__restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *s_x = reinterpret_cast<double *>(smem_raw);  // [2][cap_n]
+    double *s_xb = s_x + 2 * cap_n;                       // [2][cap_n] x_bar (FP64, prefetched)
+    double *s_qb = s_xb + 2 * cap_n;                      // [4][cap_c] q_bar (FP64, prefetched)
+    float2 *s_cell = reinterpret_cast<float2 *>(s_qb + 4 * cap_c);  // [10][cap_c]
+    float2 *s_rb = s_cell + 10 * cap_c;                   // [4][cap_c]
+    float2 *s_qi = s_rb + 4 * cap_c;                      // [4][cap_c] q_bar increments
+    float2 *s_xi = s_qi + 4 * cap_c;                      // [2][cap_n] x_bar increments
+    int *s_gc = reinterpret_cast<int *>(s_xi + 2 * cap_n);
+    int *s_gn = s_gc + cap_c;
+    const float2 *S[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S[k] = s_cell + k * cap_c;
+
+    const mp_block_desc d = desc[block0 + blockIdx.x];
+    const int tid = threadIdx.x;
+    const int nn = d.fp_count[0], nc = d.fp_count[1];
+    if ((unsigned)(reinterpret_cast<unsigned char *>(s_gn + cap_n) - smem_raw) > dynamic_smem_bytes() ||
+        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x) {
+        if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
+        return;
+    }
+    const int32_t *fpn = fp + d.fp_start[0];
+    const int32_t *fpc = fp + d.fp_start[1];
+    const bool active = tid < d.nitems;
+    ushort4 l = make_ushort4(0, 0, 0, 0);
+    int my_color = -1;
+    if (active) {
+        l = lmap[d.item_start + tid];
+        my_color = tcolor[d.item_start + tid];
+    }
+    for (int i = tid; i < nc; i += blockDim.x) {
+        const int64_t g = fpc[i];
+        dw qq[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t j = SOA ? k * ncell + g : 4 * g + k;
+            qq[k] = dw_from_double_int(q[j]);
+            stw(s_rb, k * cap_c + i, dw_from_double_int(rbar[j]));
+            s_qb[k * cap_c + i] = qbar[j];
+            s_qi[k * cap_c + i] = make_float2(0.f, 0.f);
+        }
+        const dw ri = dw_recip(qq[0]);
+        const dw u = dw_mul(qq[1], ri), v = dw_mul(qq[2], ri);
+        dw_acc A = dw_dot_begin(u, u);
+        dw_dot_add(A, v, v);
+        const dw K = dw_scale2(dw_dot_end(A), 0.5f);
+        const dw p = dw_mul(gm1, dw_sub(qq[3], dw_mul(qq[0], K)));
+        float2 *W = s_cell;
+        stw(W, 0 * cap_c + i, qq[0]);
+        stw(W, 1 * cap_c + i, qq[1]);
+        stw(W, 2 * cap_c + i, qq[2]);
+        stw(W, 3 * cap_c + i, dw_add(qq[3], p));
+        stw(W, 4 * cap_c + i, ri);
+        stw(W, 5 * cap_c + i, u);
+        stw(W, 6 * cap_c + i, v);
+        stw(W, 7 * cap_c + i, p);
+        stw(W, 8 * cap_c + i, K);
+        stw(W, 9 * cap_c + i, dw_mul(dw_from_double_int(adt[g]), half_eps));
+        s_gc[i] = (int)g;
+    }
+    for (int i = tid; i < nn; i += blockDim.x) {
+        const int64_t g = fpn[i];
+        s_x[i] = SOA ? x[g] : x[2 * g];
+        s_x[cap_n + i] = SOA ? x[nnode + g] : x[2 * g + 1];
+        s_xb[i] = SOA ? xbar[g] : xbar[2 * g];
+        s_xb[cap_n + i] = SOA ? xbar[nnode + g] : xbar[2 * g + 1];
+        s_xi[i] = make_float2(0.f, 0.f);
+        s_xi[cap_n + i] = make_float2(0.f, 0.f);
+        s_gn[i] = (int)g;
+    }
+    __syncthreads();
+    int na = 0, nb = 0, c1 = 0, c2 = 0;
+    dw qb1[4], qb2[4], nbx, nby;
+    if (active) {
+        na = l.x;
+        nb = l.y;
+        c1 = l.z;
+        c2 = l.w;
+        const dw nx = dw_from_double_int(s_x[cap_n + na] - s_x[cap_n + nb]);  // exact in FP64
+        const dw ny = dw_from_double_int(s_x[nb] - s_x[na]);
+        dw fb[4], h[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            fb[k] = dw_add_fast(ldw(s_rb, k * cap_c + c1), dw_neg(ldw(s_rb, k * cap_c + c2)));
+            h[k] = dw_scale2(fb[k], 0.5f);
+        }
+        dw_acc NX, NY;
+        flux_rev_dw(S, c1, nx, ny, h, gm1, qb1, NX, NY, true);
+        flux_rev_dw(S, c2, nx, ny, h, gm1, qb2, NX, NY, false);
+        nbx = dw_dot_end(NX);
+        nby = dw_dot_end(NY);
+        const dw mu = dw_add_fast(ldw(S[9], c1), ldw(S[9], c2));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const dw m = dw_mul(mu, fb[k]);
+            qb1[k] = dw_add_fast(qb1[k], m);
+            qb2[k] = dw_add_fast(qb2[k], dw_neg(m));
+        }
+    }
+    for (int c = 0; c < d.ncolors; ++c) {
+        if (my_color == c) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                stw(s_qi, k * cap_c + c1, dw_add_fast(ldw(s_qi, k * cap_c + c1), qb1[k]));
+                stw(s_qi, k * cap_c + c2, dw_add_fast(ldw(s_qi, k * cap_c + c2), qb2[k]));
+            }
+            // n_x = y_a - y_b, n_y = x_b - x_a
+            stw(s_xi, na, dw_add_fast(ldw(s_xi, na), dw_neg(nby)));
+            stw(s_xi, nb, dw_add_fast(ldw(s_xi, nb), nby));
+            stw(s_xi, cap_n + na, dw_add_fast(ldw(s_xi, cap_n + na), nbx));
+            stw(s_xi, cap_n + nb, dw_add_fast(ldw(s_xi, cap_n + nb), dw_neg(nbx)));
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < nc; i += blockDim.x) {
+        const int64_t g = s_gc[i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            qbar[SOA ? k * ncell + g : 4 * g + k] = f64_add_dw(s_qb[k * cap_c + i], ldw(s_qi, k * cap_c + i));
+    }
+    for (int i = tid; i < nn; i += blockDim.x) {
+        const int64_t g = s_gn[i];
+        xbar[SOA ? g : 2 * g] = f64_add_dw(s_xb[i], ldw(s_xi, i));
+        xbar[SOA ? nnode + g : 2 * g + 1] = f64_add_dw(s_xb[cap_n + i], ldw(s_xi, cap_n + i));
+    }
+}
+
+template <bool SOA>
+int adjoint_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt, const void *rbar, void *qbar,
+                 void *xbar, double gam, double eps, cudaStream_t s)
+{
+    if (P->opts.coloring != MP_COLOR_HIER || P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
+    if (P->opts.block_size > 512) return MP_EINVAL;
+    const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
+    const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
+    const int smem = cap_c * kAdjDwCellBytes + cap_n * kAdjDwNodeBytes;
+    auto kern = adjoint_hier_dw<SOA>;
+    int rc = mp_allow_smem(kern, smem);
+    if (rc != MP_OK) return rc;
+    int *err = nullptr;
+    if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
+    const double g1 = gam - 1.0, he = 0.5 * eps;
+    const float g1h = (float)g1, heh = (float)he;
+    const dw gm1{g1h, (float)(g1 - (double)g1h)}, half_eps{heh, (float)(he - (double)heh)};
+    for (int c = 0; c < P->ncolors; ++c) {
+        const int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
+        if (nb == 0) continue;
+        kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
+                                                  P->dev.tcolor, P->dev.fp, (const double *)x, (const double *)q,
+                                                  (const double *)adt, (const double *)rbar, (double *)qbar,
+                                                  (double *)xbar, nnode, ncell, cap_c, cap_n, gm1, half_eps, err);
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+}  // namespace
+
+int mp_adjoint_dw(const mp_plan *P, const void *x, const void *q, const void *adt, const void *rbar, void *qbar,
+                  void *xbar, double gam, double eps, void *stream)
+{
+    return P->opts.layout == MP_LAYOUT_SOA
+               ? adjoint_dw_t<true>(P, x, q, adt, rbar, qbar, xbar, gam, eps, as_stream(stream))
+               : adjoint_dw_t<false>(P, x, q, adt, rbar, qbar, xbar, gam, eps, as_stream(stream));
+}

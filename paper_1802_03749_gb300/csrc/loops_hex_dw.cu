@@ -39,7 +39,7 @@ __device__ __forceinline__ dw dw_det2(dw a, dw b, dw c, dw d)
 constexpr int kHexDwNodeBytes = 9 * 8 + 24 + 4;
 
 template <bool SOA>
-__global__ void __launch_bounds__(256) hex_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
+__global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
                                                    const uint4 *__restrict__ lmap, const uint8_t *__restrict__ tcolor,
                                                    const int32_t *__restrict__ fp, const double *__restrict__ x,
                                                    const double *__restrict__ v, const double *__restrict__ sig,

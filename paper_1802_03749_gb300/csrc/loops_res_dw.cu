@@ -38,7 +38,7 @@ __device__ __forceinline__ dw ld(const float2 *a, int i)
 __device__ __forceinline__ void st(float2 *a, int i, dw v) { a[i] = make_float2(v.hi, v.lo); }
 
 template <bool SOA>
-__global__ void __launch_bounds__(512, 2) res_calc_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
+__global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
                                                          const ushort4 *__restrict__ lmap,
                                                          const uint8_t *__restrict__ tcolor,
                                                          const int32_t *__restrict__ fp,

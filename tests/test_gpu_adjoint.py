@@ -21,13 +21,14 @@ def setup(nx, ny, coloring="hier", reorder="partition", layout="aos", block_size
     return m, q, adt, rb, P
 
 
-def gpu_adjoint(m, q, adt, rb, P):
+def gpu_adjoint(m, q, adt, rb, P, compute=None):
     import paper_1802_03749_gb300 as ml
     t = lambda a, w: torch.tensor(P.to_plan(a, w), dtype=torch.float64, device="cuda")
     x, qd, ad, rbd = t(m.x, "node"), t(q, "cell"), t(adt, "cell"), t(rb, "cell")
     qb = torch.zeros_like(qd)
     xb = torch.zeros_like(x)
-    ml.loop_adjoint(P.res, x, qd, ad, rbd, qb, xb)
+    ml.loop_adjoint(P.res, x, qd, ad, rbd, qb, xb, compute=compute)
+    ml.mp_check_device_status()
     torch.cuda.synchronize()
     return P.from_plan(qb.cpu().numpy(), "cell", 4), P.from_plan(xb.cpu().numpy(), "node", 2)
 
@@ -83,3 +84,25 @@ def test_autograd_function():
     qr, xr = oracle.res_calc_adjoint(m.edge2node, m.edge2cell, m.x, q, adt, rb)
     assert rel_l2(P.from_plan(qd.grad.cpu().numpy(), "cell", 4), qr) <= 1e-12
     assert rel_l2(P.from_plan(x.grad.cpu().numpy(), "node", 2), xr) <= 1e-12
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("reorder,block_size", [("partition", 128), ("rcm", 256), ("none", 480)])
+def test_adjoint_double_word_parity(reorder, block_size, layout):
+    """FP64 data with double-word arithmetic: within the FP64 bar."""
+    m, q, adt, rb, P = setup(200, 100, "hier", reorder, layout, block_size=block_size)
+    qb, xb = gpu_adjoint(m, q, adt, rb, P, compute="dw")
+    qr, xr = oracle.res_calc_adjoint(m.edge2node, m.edge2cell, m.x, q, adt, rb)
+    assert rel_l2(qb, qr) <= 1e-12
+    assert rel_l2(xb, xr) <= 1e-12
+
+
+@pytest.mark.slow
+def test_adjoint_full_size():
+    """The adjoint workload, 1200x600 quads, native FP64 and double-word."""
+    m, q, adt, rb, P = setup(1200, 600, "hier", "partition", "aos", block_size=128)
+    qr, xr = oracle.res_calc_adjoint(m.edge2node, m.edge2cell, m.x, q, adt, rb)
+    for compute in (None, "dw"):
+        qb, xb = gpu_adjoint(m, q, adt, rb, P, compute=compute)
+        assert rel_l2(qb, qr) <= 1e-12
+        assert rel_l2(xb, xr) <= 1e-12
