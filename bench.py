@@ -238,13 +238,15 @@ def bench_rows(ml, torch, timer, args):
     """Measurements of the other loops (not the headline): hex assembly,
     the adjoint and the batched graph-captured time step (``--rows``)."""
     rows = {}
-    want = set(args.rows.split(",")) if args.rows else set()
+    want = set(args.rows.split(",")) if args.rows and args.rows != "none" else set()
     if "hex" in want:
         rows.update(bench_hex(ml, torch, timer, args))
     if "adjoint" in want:
         rows.update(bench_adjoint(ml, torch, timer, args))
     if "batch" in want:
         rows.update(bench_batch(ml, torch, timer, args))
+    if "shapes" in want:
+        rows.update(bench_shapes(ml, torch, timer, args))
     return rows
 
 
@@ -259,7 +261,8 @@ def bench_hex(ml, torch, timer, args):
         tdt = torch.float64 if dtype == "f64" else torch.float32
         elt = 8 if dtype == "f64" else 4
         for coloring, reorder, variant in (("hier", "partition", "simple"), ("hier", "partition", "smem_atomic"),
-                                           ("atomic", "rcm", None), ("global", "rcm", None)):
+                                           ("atomic", "rcm", None), ("global", "rcm", None),
+                                           ("twostep", "rcm", None)):
             H = HexPlan(hm.nnode, hm.elem2node, block_size=256, reorder=reorder, coloring=coloring, staged=variant)
             H.plan.upload()
             x = torch.tensor(H.to_plan(hm.x, "node"), dtype=tdt, device="cuda")
@@ -292,6 +295,40 @@ def bench_hex(ml, torch, timer, args):
         "gelems_s": hm.nelem / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
         "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"], "reuse": st["reuse_all"]}
     del x, vd, sd, f, vol
+    return rows
+
+
+def bench_shapes(ml, torch, timer, args):
+    """Handcrafted block shapes on a structured hex grid (Sec. 3.1.6): 128
+    elements per block as 1D lines, 2D slabs or 3D bricks, against the
+    partitioner and RCM chunks, on a 128 x 64 x 64 grid the shapes tile."""
+    from paper_1802_03749_gb300.mesh import HexPlan
+    dims = (128, 64, 64)
+    hm = meshgen.hex_mesh(dims[0], nyz=dims[1:])
+    sig, v = meshgen.hex_fields(hm)
+    rows = {}
+    layouts = {"line_128x1x1": (128, 1, 1), "slab_16x8x1": (16, 8, 1), "brick_8x4x4": (8, 4, 4),
+               "partition": None, "rcm": None}
+    for name, shape in layouts.items():
+        blk = meshgen.hex_bricks(hm, shape, dims) if shape else None
+        reorder = "rcm" if name == "rcm" else "partition"
+        for comp, staged in ((None, "smem_atomic"), (None, "simple"), ("dw", None)):
+            H = HexPlan(hm.nnode, hm.elem2node, block_size=128, reorder=reorder, coloring="hier", staged=staged,
+                        block_of=blk)
+            H.plan.upload()
+            tdt = torch.float32 if comp is None else torch.float64
+            x = torch.tensor(H.to_plan(hm.x, "node"), dtype=tdt, device="cuda")
+            vd = torch.tensor(H.to_plan(v, "node"), dtype=tdt, device="cuda")
+            sd = torch.tensor(H.to_plan(sig, "elem"), dtype=tdt, device="cuda")
+            f = torch.zeros_like(x)
+            vol = torch.zeros(hm.nelem, dtype=tdt, device="cuda")
+            ms, _ = timer(lambda: ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01, compute=comp), 10, 2)
+            st = H.plan.stats()
+            key = f"hex_shape_{name}_" + ("f64dw" if comp else f"f32_{staged}")
+            rows[key] = {"workload": "hex assembly 128x64x64, blocks of 128", "ms": ms,
+                         "gelems_s": hm.nelem / ms / 1e6, "reuse": st["reuse_all"],
+                         "thread_colors_mean": st["mean_thread_colors"], "block_colors": st["nblock_colors"]}
+            del x, vd, sd, f, vol
     return rows
 
 
@@ -364,11 +401,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--layout", default="aos", choices=["aos", "soa"])
+    ap.add_argument("--staged", default=None, choices=["simple", "gather", "smem_atomic", "pipelined"],
+                    help="increment form of the staged headline kernel (default: the library's)")
     ap.add_argument("--compute", default="dw", choices=["dw", "f64", "f32"],
                     help="dw: FP64 data with double-word arithmetic; f64: native FP64; f32: FP32 data")
     ap.add_argument("--no-variants", action="store_true", help="skip the baseline variants")
-    ap.add_argument("--rows", default="hex,adjoint,batch",
-                    help="other loops to measure (comma list of hex, adjoint, batch; empty for none)")
+    ap.add_argument("--rows", default="hex,adjoint,batch,shapes",
+                    help="other loops to measure (comma list of hex, adjoint, batch, shapes; none for none)")
     ap.add_argument("--no-rows", action="store_true", help="skip the hex / adjoint / batch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--nx", type=int, default=NX, help="quad grid size (profiling runs use smaller meshes)")
@@ -402,9 +441,9 @@ def main():
     useful = useful_bytes_res_calc(m.ncell, m.nnode, m.nedge, elt)
     hbm_peak, peak_kind = read_peaks()
 
-    def setup(coloring, reorder, layout=args.layout, bs=args.block_size):
+    def setup(coloring, reorder, layout=args.layout, bs=args.block_size, staged=None):
         P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                         block_size=bs, reorder=reorder, coloring=coloring, layout=layout)
+                         block_size=bs, reorder=reorder, coloring=coloring, layout=layout, staged=staged)
         P.res.upload()
         d = {"x": torch.tensor(P.to_plan(m.x, "node"), dtype=tdt, device="cuda"),
              "q": torch.tensor(P.to_plan(q, "cell"), dtype=tdt, device="cuda"),
@@ -413,7 +452,7 @@ def main():
         return P, d
 
     # ---------------------------------------------------------- headline
-    P, d = setup("hier", "partition")
+    P, d = setup("hier", "partition", staged=args.staged)
     st = P.res.stats()
     step = lambda: ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS, compute=compute)
     clk = ClockSampler(local)
@@ -459,20 +498,25 @@ def main():
     del d
 
     # ---------------------------------------------------------- variants
-    variants = {"two_layer_partition" + ("_dw" if compute else ""): {
+    head_name = "two_layer_partition" + ("_dw" if compute else "") + (f"_{args.staged}" if args.staged else "")
+    variants = {head_name: {
         "gedges_s": value / world, "ms": ms_step, "useful_gbs": gbs, "block_colors": st["nblock_colors"],
         "thread_colors_mean": st["mean_thread_colors"], "reuse": st["reuse_all"],
         "plan_seconds": st["seconds_total"]}}
     if not args.no_variants:
         ks = max(5, args.steps // 2)
-        todo = [("two_layer_rcm", "hier", "rcm", compute), ("global_rcm", "global", "rcm", None),
-                ("global_none", "global", "none", None), ("atomic_rcm", "atomic", "rcm", None),
-                ("atomic_none", "atomic", "none", None)]
+        other = "gather" if args.staged != "gather" else None
+        todo = [("two_layer_partition" + ("_dw" if compute else "") + f"_{other or 'colour'}", "hier", "partition",
+                 compute, other),
+                ("two_layer_rcm", "hier", "rcm", compute, args.staged), ("global_rcm", "global", "rcm", None, None),
+                ("global_none", "global", "none", None, None), ("atomic_rcm", "atomic", "rcm", None, None),
+                ("atomic_none", "atomic", "none", None, None), ("twostep_rcm", "twostep", "rcm", None, None)]
         if compute == "dw":
-            todo.insert(0, ("two_layer_partition_native_f64", "hier", "partition", None))
-        for name, coloring, reorder, comp in todo:
+            todo.insert(1, ("two_layer_partition_native_f64", "hier", "partition", None, None))
+            todo.insert(2, ("two_layer_partition_native_f64_gather", "hier", "partition", None, "gather"))
+        for name, coloring, reorder, comp, stg in todo:
             try:
-                Pv, dv = setup(coloring, reorder)
+                Pv, dv = setup(coloring, reorder, staged=stg)
             except ml.MeshLoopError as e:
                 variants[name] = {"error": str(e)}
                 continue
@@ -501,7 +545,9 @@ def main():
             "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, "
                                    + ("FP32 data" if f32 else "FP64 data")
                                    + (", double-word arithmetic" if compute else "")
-                                   + f", two-layer colouring, RCM + partition, block {args.block_size}, "
+                                   + f", two-layer colouring"
+                                   + (f" ({args.staged} increments)" if args.staged else "")
+                                   + f", RCM + partition, block {args.block_size}, "
                                    + args.layout.upper(),
                        "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (useful bytes {useful / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB)"},

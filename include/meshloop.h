@@ -73,7 +73,13 @@ extern "C" {
 
 /* ------------------------------------------------------------- options */
 enum { MP_REORDER_NONE = 0, MP_REORDER_RCM = 1, MP_REORDER_PARTITION = 2 };
-enum { MP_COLOR_HIER = 0, MP_COLOR_GLOBAL = 1, MP_COLOR_ATOMIC = 2 };
+enum { MP_COLOR_HIER = 0, MP_COLOR_GLOBAL = 1, MP_COLOR_ATOMIC = 2, MP_COLOR_TWOSTEP = 3 };
+/* MP_COLOR_TWOSTEP (Sec. 2.1, the temporary-array method): a first kernel
+ * writes every iteration's increments to a scratch array of from_size x
+ * arity x dim values; a second kernel gathers them per point of the written
+ * to-set through the inverse map (fixed order, deterministic).  Plans with
+ * exactly one written map; the library allocates the scratch on the first
+ * loop call and frees it with the plan.                                  */
 enum { MP_LAYOUT_AOS = 0, MP_LAYOUT_SOA = 1 };
 enum { MP_F64 = 0, MP_F32 = 1, MP_F64_DW = 2 };
 /* MP_F64_DW: FP64 data, arithmetic in double-word (pairs of FP32, ~48-bit
@@ -109,6 +115,12 @@ typedef struct {
                             default (MP_STAGED_SMEM_ATOMIC for hex assembly, whose 3D
                             blocks need ~10 thread colours; MP_STAGED_SIMPLE otherwise) */
     int32_t pad_;
+    const int32_t *block_of; /* optional, host, from_size entries: caller-defined
+                            blocks (e.g. handcrafted shapes on a structured mesh,
+                            Sec. 3.1.6).  Iterations with equal values form one block
+                            (ascending value order, iterations ascending inside); no
+                            reordering or partitioning is applied; each block must
+                            hold at most block_size iterations (else MP_EINVAL).     */
 } mp_plan_opts;
 
 /* Fill opts with defaults: S = 512, PARTITION, HIER, AOS, l = 1.001,
@@ -169,10 +181,21 @@ int mesh_plan_perm(const mp_plan *plan, int32_t set_id, int32_t *new_to_old);
  *   MP_TAB_LOCAL_MAP      int32[from_size*stride] HIER: block-local index of
  *                                     every map slot (maps in order, padded
  *                                     to stride = 4, 8 or 16 entries)
+ *   MP_TAB_GATHER         int32[len(MP_TAB_FOOTPRINT) * W] HIER: per
+ *                                     footprint point a row of W (4, 8 or 16;
+ *                                     count 0 when some point of a block has
+ *                                     more than 16 increments) entries: block-
+ *                                     local iteration * 16 + map slot of each
+ *                                     increment of the point, ascending, then
+ *                                     -1 padding
+ *   MP_TAB_INV_OFFSETS    int32[to_size+1] TWOSTEP: range of each point of
+ *                                     the written to-set in MP_TAB_INV_INDEX
+ *   MP_TAB_INV_INDEX      int32[from_size*arity] TWOSTEP: item*arity + slot
  * Iterations are in plan numbering.                                       */
 enum { MP_TAB_BLOCK_OFFSETS = 0, MP_TAB_COLOR_OFFSETS = 1, MP_TAB_BLOCK_COLOR = 2,
        MP_TAB_THREAD_COLOR = 3, MP_TAB_MAP = 4, MP_TAB_FOOTPRINT = 5, MP_TAB_FP_START = 6,
-       MP_TAB_FP_COUNT = 7, MP_TAB_LOCAL_MAP = 8 };
+       MP_TAB_FP_COUNT = 7, MP_TAB_LOCAL_MAP = 8, MP_TAB_INV_OFFSETS = 9, MP_TAB_INV_INDEX = 10,
+       MP_TAB_GATHER = 11 };
 int mesh_plan_table(const mp_plan *plan, int32_t table, int32_t arg, int32_t *out, int64_t cap,
                     int64_t *count);
 
@@ -232,7 +255,12 @@ int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void 
  *    order of additions, and so the rounding, is not fixed).  Not for the
  *    double-word res_calc or the adjoint, which run SIMPLE.
  * Block colouring orders the write-back in every variant.                */
-enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2 };
+enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2, MP_STAGED_GATHER = 3 };
+/* MP_STAGED_GATHER: no thread colours: each thread stores its iteration's
+ * increments in shared memory, one barrier, then every footprint point sums
+ * the increments of its iterations in the block (block-local inverse map,
+ * fixed order: deterministic) and writes back once.  res_calc (native and
+ * double-word).                                                          */
 
 /* Far-field boundary flux bres_calc over boundary edges: with
  * q_b = (q_c + qinf)/2,  res[c] += F(q_b).n + eps adt_c (q_c - qinf).

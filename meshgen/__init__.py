@@ -303,6 +303,21 @@ def hex_mesh(n: int, seed: int = DEFAULT_SEED, jitter: float = 0.2, permute: boo
     return HexMesh(n, h, np.ascontiguousarray(x), np.ascontiguousarray(elem2node, dtype=np.int32), perms)
 
 
+def hex_bricks(mesh: HexMesh, shape: tuple, dims: tuple) -> np.ndarray:
+    """Block id of every element (in the mesh's numbering) for handcrafted
+    brick-shaped blocks of shape = (bx, by, bz) elements on a structured grid
+    of dims = (nx, ny, nz) elements: element (i, j, k) belongs to brick
+    (i // bx, j // by, k // bz), numbered x fastest."""
+    nx, ny, nz = dims
+    bx, by, bz = shape
+    orig = mesh.perms.get("elem", np.arange(mesh.nelem))
+    i = orig % nx
+    j = (orig // nx) % ny
+    k = orig // (nx * ny)
+    gx, gy = -(-nx // bx), -(-ny // by)
+    return ((k // bz) * gy + (j // by)) * gx + (i // bx)
+
+
 def hex_fields(mesh: HexMesh, seed: int = DEFAULT_SEED):
     """Element stresses sig = diag(sxx, syy, szz) ~ U(-1.5, -0.5) and nodal
     velocities v = A x + b + 0.1 N(0,1), with A, b ~ U(-1, 1)."""

@@ -35,12 +35,12 @@ MP_MAX_BLOCK_COLORS = 256
 MP_MAX_MAPS = 4
 MP_MAX_TOSETS = 2
 REORDER = {"none": 0, "rcm": 1, "partition": 2}
-STAGED = {None: -1, "pipelined": 0, "simple": 1, "smem_atomic": 2}
-COLORING = {"hier": 0, "global": 1, "atomic": 2}
+STAGED = {None: -1, "pipelined": 0, "simple": 1, "smem_atomic": 2, "gather": 3}
+COLORING = {"hier": 0, "global": 1, "atomic": 2, "twostep": 3}
 LAYOUT = {"aos": 0, "soa": 1}
 DTYPE = {"f64": 0, "f32": 1, "f64dw": 2}
 TABLES = {"block_offsets": 0, "color_offsets": 1, "block_color": 2, "thread_color": 3, "map": 4,
-          "footprint": 5, "fp_start": 6, "fp_count": 7, "local_map": 8}
+          "footprint": 5, "fp_start": 6, "fp_count": 7, "local_map": 8, "inv_offsets": 9, "inv_index": 10, "gather": 11}
 
 
 class MeshLoopError(RuntimeError):
@@ -60,7 +60,7 @@ class mp_plan_opts(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("reorder", ctypes.c_int32), ("coloring", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("imbalance", ctypes.c_double), ("eps", ctypes.c_double),
                 ("primary_map", ctypes.c_int32), ("data_reorder", ctypes.c_int32), ("staged", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("pad_", ctypes.c_int32), ("block_of", ctypes.c_void_p)]
 
 
 class mp_plan_stats(ctypes.Structure):
@@ -148,7 +148,8 @@ class Plan:
 
     def __init__(self, maps, from_size: int, block_size: int = 512, reorder: str = "partition",
                  coloring: str = "hier", layout: str = "aos", imbalance: float = 1.001, eps: float = 0.0,
-                 primary_map: int = -1, data_reorder: int = -1, staged: str | None = None, _handle=None):
+                 primary_map: int = -1, data_reorder: int = -1, staged: str | None = None, block_of=None,
+                 _handle=None):
         L = lib()
         self._h = ctypes.c_void_p()
         if _handle is not None:
@@ -175,6 +176,10 @@ class Plan:
         o.primary_map = int(primary_map)
         o.data_reorder = int(data_reorder)
         o.staged = STAGED[staged]
+        if block_of is not None:
+            bo = np.ascontiguousarray(block_of, dtype=np.int32)
+            keep.append(bo)
+            o.block_of = bo.ctypes.data
         _check(L.mesh_plan_build(arr, n, int(from_size), ctypes.byref(o), ctypes.byref(self._h)),
                "mesh_plan_build")
         self.maps_meta = [(int(m["to_set"]), int(m["to_size"])) for m in maps]

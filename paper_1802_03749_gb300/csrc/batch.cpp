@@ -87,6 +87,26 @@ extern "C" int mesh_batch_build(const mp_plan *const *plans, int32_t n, mp_plan 
             }
         }
         if (acc > INT32_MAX) throw std::bad_alloc();
+        // gather rows follow the same concatenation, widened to the widest
+        B->gat_w = 0;
+        for (int k = 0; k < n; ++k) B->gat_w = std::max(B->gat_w, plans[k]->gat_w);
+        for (int k = 0; k < n; ++k)
+            if (plans[k]->gat_w == 0) B->gat_w = 0;
+        if (B->gat_w > 0) {
+            B->gat_tab.assign((size_t)acc * B->gat_w, 0xFFFF);
+            for (int k = 0; k < n; ++k) {
+                const mp_plan &P = *plans[k];
+                int64_t own = 0;
+                for (int s = 0; s < B->ntosets; ++s) {
+                    const int64_t npt = (int64_t)P.fp_ids[s].size();
+                    for (int64_t i = 0; i < npt; ++i)
+                        for (int w = 0; w < P.gat_w; ++w)
+                            B->gat_tab[(size_t)(slot_base[s][k] + i) * B->gat_w + w] =
+                                P.gat_tab[(size_t)(own + i) * P.gat_w + w];
+                    own += npt;
+                }
+            }
+        }
         // blocks grouped by colour phase, meshes in order inside a phase; the
         // iterations of the union are renumbered to follow that block order,
         // so every block is a contiguous iteration range

@@ -51,6 +51,12 @@ int mp_res_calc_pipe(const mp_plan *P, int32_t dtype, const void *x, const void 
                      double gam, double eps, void *stream);
 // Staged implementation of a HIER plan: opts.staged, or the loop default.
 inline int mp_staged(const mp_plan *P, int loop_default) { return P->opts.staged < 0 ? loop_default : P->opts.staged; }
+// the plan carries (and has uploaded) a gather table of at most 16 entries
+// per footprint point; plans without one run the thread-coloured form
+inline bool mp_gather_ready(const mp_plan *P)
+{
+    return P->gat_w >= 4 && P->gat_w <= 16 && P->dev.gat != nullptr;
+}
 
 // Two-layer res_calc with FP64 data and double-word arithmetic.
 int mp_res_calc_dw(const mp_plan *P, const void *x, const void *q, const void *adt, void *res, double gam, double eps,
@@ -63,6 +69,11 @@ int mp_hex_dw(const mp_plan *P, const void *x, const void *v, const void *sig, v
 // Two-layer res_calc adjoint with FP64 data and double-word arithmetic.
 int mp_adjoint_dw(const mp_plan *P, const void *x, const void *q, const void *adt, const void *rbar, void *qbar,
                   void *xbar, double gam, double eps, void *stream);
+
+// TWOSTEP plans: the per-(item, slot) increment scratch (allocated on first
+// use, kept with the plan) and the gather of step 2 into out (+=).
+int mp_twostep_scratch(const mp_plan *P, size_t bytes, void **out);
+int mp_twostep_gather(const mp_plan *P, int32_t dtype, int dim, const void *scratch, void *out, void *stream);
 
 // Library-owned device scratch for deterministic reductions (per device).
 int mp_reduce_scratch(double **partials, int *nparts);

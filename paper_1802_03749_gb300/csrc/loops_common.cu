@@ -32,7 +32,11 @@ void mp_plan_free_device(mp_plan *P)
     cudaFree(d.lmap);
     cudaFree(d.fp);
     cudaFree(d.tcolor);
+    cudaFree(d.gat);
     for (auto &m : d.map) cudaFree(m);
+    cudaFree(d.inv_off);
+    cudaFree(d.inv_idx);
+    cudaFree(d.scratch);
     if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
     d = mp_device_tables{};
 }
@@ -63,9 +67,16 @@ int mp_plan_ensure_device(const mp_plan *cplan)
             for (int s = 0; s < P->ntosets; ++s) all.insert(all.end(), P->fp_ids[s].begin(), P->fp_ids[s].end());
             if ((rc = upload(&d.fp, all.data(), all.size(), bytes)) != MP_OK) goto fail;
         }
+        if (!P->gat_tab.empty() &&
+            (rc = upload(&d.gat, P->gat_tab.data(), P->gat_tab.size(), bytes)) != MP_OK)
+            goto fail;
     } else {
         for (int m = 0; m < P->nmaps; ++m)
             if ((rc = upload(&d.map[m], P->maps[m].idx.data(), P->maps[m].idx.size(), bytes)) != MP_OK) goto fail;
+        if (P->opts.coloring == MP_COLOR_TWOSTEP) {
+            if ((rc = upload(&d.inv_off, P->inv_off.data(), P->inv_off.size(), bytes)) != MP_OK) goto fail;
+            if ((rc = upload(&d.inv_idx, P->inv_idx.data(), P->inv_idx.size(), bytes)) != MP_OK) goto fail;
+        }
     }
     d.device = dev;
     d.bytes = bytes;
@@ -284,6 +295,73 @@ extern "C" int loop_update_noalloc(int64_t ncell, int32_t dtype, int32_t layout,
         k<<<nparts, 256, 0, s>>>((const float *)qold, (float *)q, (float *)res, (const float *)adt, ncell, parts);
     }
     sum_partials_kernel<<<1, 256, 0, s>>>(parts, nparts, rms_dev);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+// ----------------------------------------------------- two-step gather
+
+int mp_twostep_scratch(const mp_plan *cplan, size_t bytes, void **out)
+{
+    mp_plan *P = const_cast<mp_plan *>(cplan);
+    mp_device_tables &d = P->dev;
+    if (d.scratch_bytes < bytes) {
+        if (d.scratch) MP_CUDA_TRY(cudaFree(d.scratch));
+        d.scratch = nullptr;
+        d.scratch_bytes = 0;
+        MP_CUDA_TRY(cudaMalloc(&d.scratch, bytes));
+        d.scratch_bytes = bytes;
+    }
+    *out = d.scratch;
+    return MP_OK;
+}
+
+namespace {
+
+// Step 2 of the temporary-array method: each point of the written to-set
+// sums its (item, slot) increments in inverse-map order and adds them once.
+template <typename T, int DIM, bool SOA>
+__global__ void __launch_bounds__(256) twostep_gather(const int32_t *__restrict__ inv_off,
+                                                      const int32_t *__restrict__ inv_idx,
+                                                      const T *__restrict__ scratch, T *__restrict__ out, int64_t n)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    T acc[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) acc[k] = T(0);
+    for (int j = inv_off[p]; j < inv_off[p + 1]; ++j) {
+        const int64_t base = (int64_t)inv_idx[j] * DIM;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) acc[k] += scratch[base + k];
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) out[SOA ? k * n + p : p * DIM + k] += acc[k];
+}
+
+template <typename T, int DIM>
+void launch_gather(const mp_plan *P, const void *scratch, void *out, cudaStream_t s)
+{
+    const int64_t n = P->maps[P->inv_map].to_size;
+    const int grid = (int)((n + 255) / 256);
+    if (P->opts.layout == MP_LAYOUT_SOA)
+        twostep_gather<T, DIM, true><<<grid, 256, 0, s>>>(P->dev.inv_off, P->dev.inv_idx, (const T *)scratch, (T *)out, n);
+    else
+        twostep_gather<T, DIM, false><<<grid, 256, 0, s>>>(P->dev.inv_off, P->dev.inv_idx, (const T *)scratch, (T *)out,
+                                                           n);
+}
+
+}  // namespace
+
+int mp_twostep_gather(const mp_plan *P, int32_t dtype, int dim, const void *scratch, void *out, void *stream)
+{
+    cudaStream_t s = as_stream(stream);
+    if (dim == 4)
+        dtype == MP_F64 ? launch_gather<double, 4>(P, scratch, out, s) : launch_gather<float, 4>(P, scratch, out, s);
+    else if (dim == 3)
+        dtype == MP_F64 ? launch_gather<double, 3>(P, scratch, out, s) : launch_gather<float, 3>(P, scratch, out, s);
+    else
+        return MP_EINVAL;
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

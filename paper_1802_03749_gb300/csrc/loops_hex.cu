@@ -262,6 +262,36 @@ __global__ void __launch_bounds__(256) hex_direct(int e0, int e1, const int32_t 
         }
 }
 
+// Step 1 of the temporary-array method (Sec. 2.1): element e's force on
+// its corner i goes to scratch[(8e + i) * 3 + a]; vol is written directly.
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(256) hex_step1(int n, const int32_t *__restrict__ e2n, const T *__restrict__ x,
+                                                 const T *__restrict__ v, const T *__restrict__ sig,
+                                                 T *__restrict__ scratch, T *__restrict__ vol, int64_t nnode,
+                                                 int64_t nelem, T kappa)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int4 *row = reinterpret_cast<const int4 *>(e2n) + 2 * (int64_t)e;
+    int4 r0 = row[0], r1 = row[1];
+    const int nd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    T xe[8][3], ve[8][3], fe[8][3];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        load3<T, SOA>(x, nnode, nd[i], xe[i][0], xe[i][1], xe[i][2]);
+        load3<T, SOA>(v, nnode, nd[i], ve[i][0], ve[i][1], ve[i][2]);
+    }
+    T s0, s1, s2, V;
+    load3<T, SOA>(sig, nelem, e, s0, s1, s2);
+    hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
+    vol[e] = V;
+    T *o = scratch + 24 * (int64_t)e;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) o[3 * i + a] = fe[i][a];
+}
+
 template <typename T, bool SOA>
 int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol,
                     double kappa, cudaStream_t s)
@@ -284,6 +314,15 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
                                                       P->dev.tcolor, P->dev.fp, (const T *)x, (const T *)v,
                                                       (const T *)sig, (T *)f, (T *)vol, nnode, nelem, cap, (T)kappa, err);
         }
+    } else if (P->opts.coloring == MP_COLOR_TWOSTEP) {
+        void *scratch = nullptr;
+        int rc = mp_twostep_scratch(P, (size_t)nelem * 24 * sizeof(T), &scratch);
+        if (rc != MP_OK) return rc;
+        const int n = (int)nelem;
+        hex_step1<T, SOA><<<(n + 255) / 256, 256, 0, s>>>(n, P->dev.map[0], (const T *)x, (const T *)v, (const T *)sig,
+                                                           (T *)scratch, (T *)vol, nnode, nelem, (T)kappa);
+        MP_CUDA_TRY(cudaGetLastError());
+        return mp_twostep_gather(P, sizeof(T) == 8 ? MP_F64 : MP_F32, 3, scratch, f, s);
     } else {
         const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;
         for (int c = 0; c < P->ncolors; ++c) {

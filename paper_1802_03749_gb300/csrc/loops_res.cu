@@ -20,10 +20,20 @@ namespace {
 // ------------------------------------------------------------------ HIER
 
 // Dynamic shared memory layout for a block with cap_c cells and cap_n nodes:
+//   ushort4 ge[gw4][cap_c]   (gather form only: the cell's increment list)
 //   T  q[4][cap_c], adt[cap_c], u[cap_c], v[cap_c], p[cap_c], H[cap_c]
 //   T  inc[4][cap_c]         (res prefetched at staging, increments added on)
 //   T  xh[2][cap_n]          (half coordinates, n/2 = differences of these)
+//   T  f[4][cap_f]           (gather form only: one flux per thread)
 //   int gid[cap_c]
+//
+// Increment forms (template INC):
+//   kIncColor   thread colours, one colour per barrier (Algorithm 1)
+//   kIncAtomic  shared-memory atomics, one barrier
+//   kIncGather  every thread stores its flux, one barrier, then each cell
+//               sums the fluxes of its edges in the block from the plan's
+//               block-local inverse map (fixed order: deterministic) and is
+//               written back by the same thread
 template <typename T>
 __host__ __device__ constexpr int res_smem_per_cell()
 {
@@ -34,6 +44,7 @@ __host__ __device__ constexpr int res_smem_per_node()
 {
     return 2 * (int)sizeof(T);
 }
+constexpr int kIncColor = 0, kIncAtomic = 1, kIncGather = 2;
 
 template <typename T, bool SOA>
 __device__ __forceinline__ void load_res(const T *__restrict__ res, int64_t ncell, int g, T &r0, T &r1, T &r2, T &r3)
@@ -59,17 +70,19 @@ __device__ __forceinline__ void load_res(const T *__restrict__ res, int64_t ncel
     }
 }
 
-template <typename T, bool SOA, bool SMEM_ATOMIC>
+template <typename T, bool SOA, int INC>
 __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__restrict__ desc, int block0,
                                                       const ushort4 *__restrict__ lmap,
                                                       const uint8_t *__restrict__ tcolor,
+                                                      const ushort4 *__restrict__ gat, int gw4,
                                                       const int32_t *__restrict__ fp, const T *__restrict__ x,
                                                       const T *__restrict__ q, const T *__restrict__ adt,
                                                       T *__restrict__ res, int64_t nnode, int64_t ncell, int cap_c,
-                                                      int cap_n, T gm1, T half_eps, int *__restrict__ err)
+                                                      int cap_n, int cap_f, T gm1, T half_eps, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s_q = reinterpret_cast<T *>(smem_raw);
+    ushort4 *s_ge = reinterpret_cast<ushort4 *>(smem_raw);
+    T *s_q = reinterpret_cast<T *>(s_ge + (INC == kIncGather ? gw4 * cap_c : 0));
     T *s_adt = s_q + 4 * cap_c;
     T *s_u = s_adt + cap_c;
     T *s_v = s_u + cap_c;
@@ -77,7 +90,8 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     T *s_H = s_p + cap_c;
     T *s_inc = s_H + cap_c;
     T *s_xh = s_inc + 4 * cap_c;
-    int *s_gid = reinterpret_cast<int *>(s_xh + 2 * cap_n);
+    T *s_f = s_xh + 2 * cap_n;
+    int *s_gid = reinterpret_cast<int *>(s_f + (INC == kIncGather ? 4 * cap_f : 0));
 
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
@@ -85,7 +99,8 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     // the carve-up above must fit the launch's dynamic shared memory and
     // the block's footprint its capacity; otherwise record and return
     if ((unsigned)(reinterpret_cast<unsigned char *>(s_gid + cap_c) - smem_raw) > dynamic_smem_bytes() ||
-        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x) {
+        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x ||
+        (INC == kIncGather && ((int)blockDim.x > cap_f || gw4 < 1 || gw4 > 4))) {
         if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
         return;
     }
@@ -98,7 +113,7 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     int my_color = -1;
     if (active) {
         l = lmap[d.item_start + tid];
-        my_color = tcolor[d.item_start + tid];
+        if (INC == kIncColor) my_color = tcolor[d.item_start + tid];
     }
 
     // stage cells: q, adt, per-cell primitives and the current res
@@ -145,6 +160,10 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         s_inc[2 * cap_c + i] = r2;
         s_inc[3 * cap_c + i] = r3;
         s_gid[i] = g;
+        if (INC == kIncGather) {
+            const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
+            for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];
+        }
     }
     // stage nodes as half coordinates (exact scaling by 1/2)
     for (int i = tid; i < nn; i += blockDim.x) {
@@ -179,7 +198,49 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
                   s_p[c1], s_H[c1], s_adt[c1], s_q[c2], s_q[cap_c + c2], s_q[2 * cap_c + c2], s_q[3 * cap_c + c2],
                   s_u[c2], s_v[c2], s_p[c2], s_H[c2], s_adt[c2], half_eps, f);
     }
-    if (SMEM_ATOMIC) {
+    if constexpr (INC == kIncGather) {
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_f[k * cap_f + tid] = f[k];
+        }
+        __syncthreads();
+        // each cell: prefetched res plus its edges' fluxes (+f from the
+        // edge's first cell slot, -f from its second), then one store
+        for (int i = tid; i < nc; i += blockDim.x) {
+            T a[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[k] = s_inc[k * cap_c + i];
+            for (int h = 0; h < gw4; ++h) {
+                const ushort4 e4 = s_ge[h * cap_c + i];
+                const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned e = es[j];
+                    if (e == 0xFFFFu) continue;
+                    const int t = (int)(e >> 4);
+                    const bool neg = (e & 15u) == 3u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const T v = s_f[k * cap_f + t];
+                        a[k] = neg ? a[k] - v : a[k] + v;
+                    }
+                }
+            }
+            const int g = s_gid[i];
+            if (SOA) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) res[k * ncell + g] = a[k];
+            } else if (sizeof(T) == 8) {
+                double2 *r2 = reinterpret_cast<double2 *>(res) + 2 * (int64_t)g;
+                r2[0] = make_double2((double)a[0], (double)a[1]);
+                r2[1] = make_double2((double)a[2], (double)a[3]);
+            } else {
+                reinterpret_cast<float4 *>(res)[g] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+            }
+        }
+        return;
+    }
+    if (INC == kIncAtomic) {
         // shared-memory atomics instead of thread colours: one barrier
         if (active) {
 #pragma unroll
@@ -303,6 +364,39 @@ __global__ void __launch_bounds__(256) res_calc_direct(int e0, int e1, const int
     }
 }
 
+// Step 1 of the temporary-array method (Sec. 2.1): the increments of edge
+// e for its two cells go to scratch[(2e + slot) * 4 + k] (+f, -f).
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(256) res_calc_step1(int n, const int32_t *__restrict__ e2n,
+                                                      const int32_t *__restrict__ e2c, const T *__restrict__ x,
+                                                      const T *__restrict__ q, const T *__restrict__ adt,
+                                                      T *__restrict__ scratch, int64_t nnode, int64_t ncell, T gm1,
+                                                      T half_eps)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int2 nab = reinterpret_cast<const int2 *>(e2n)[e];
+    int2 cc = reinterpret_cast<const int2 *>(e2c)[e];
+    T xa, ya, xb, yb;
+    load_node<T, SOA>(x, nnode, nab.x, xa, ya);
+    load_node<T, SOA>(x, nnode, nab.y, xb, yb);
+    T r1, ru1, rv1, E1, r2, ru2, rv2, E2;
+    load_cell<T, SOA>(q, ncell, cc.x, r1, ru1, rv1, E1);
+    load_cell<T, SOA>(q, ncell, cc.y, r2, ru2, rv2, E2);
+    T u1, v1, p1, H1, u2, v2, p2, H2;
+    cell_prims(r1, ru1, rv1, E1, gm1, u1, v1, p1, H1);
+    cell_prims(r2, ru2, rv2, E2, gm1, u2, v2, p2, H2);
+    T f[4];
+    edge_flux(T(0.5) * ya - T(0.5) * yb, T(0.5) * xb - T(0.5) * xa, r1, ru1, rv1, E1, u1, v1, p1, H1, adt[cc.x], r2,
+              ru2, rv2, E2, u2, v2, p2, H2, adt[cc.y], half_eps, f);
+    T *o = scratch + 8 * (int64_t)e;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        o[k] = f[k];
+        o[4 + k] = -f[k];
+    }
+}
+
 // ------------------------------------------------------------- bres_calc
 
 // Far-field boundary edges: q_b = (q_c + qinf)/2,
@@ -399,9 +493,14 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
     if (co == MP_COLOR_HIER) {
         if (P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
         const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
-        const int smem = cap_c * res_smem_per_cell<T>() + cap_n * res_smem_per_node<T>();
-        auto kern = mp_staged(P, MP_STAGED_SIMPLE) == MP_STAGED_SMEM_ATOMIC ? res_calc_hier<T, SOA, true>
-                                                                            : res_calc_hier<T, SOA, false>;
+        const int variant = mp_staged(P, MP_STAGED_SIMPLE);
+        const bool gather = variant == MP_STAGED_GATHER && mp_gather_ready(P);
+        const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
+        const int smem = cap_c * res_smem_per_cell<T>() + cap_n * res_smem_per_node<T>() + gw4 * cap_c * 8 +
+                         4 * cap_f * (int)sizeof(T);
+        auto kern = gather                                 ? res_calc_hier<T, SOA, kIncGather>
+                    : variant == MP_STAGED_SMEM_ATOMIC ? res_calc_hier<T, SOA, kIncAtomic>
+                                                       : res_calc_hier<T, SOA, kIncColor>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
         int *err = nullptr;
@@ -411,9 +510,20 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
             int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
             if (nb == 0) continue;
             kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
-                                                      P->dev.tcolor, fp, (const T *)x, (const T *)q, (const T *)adt,
-                                                      (T *)res, nnode, ncell, cap_c, cap_n, gm1, half_eps, err);
+                                                      P->dev.tcolor, reinterpret_cast<const ushort4 *>(P->dev.gat),
+                                                      gw4, fp, (const T *)x, (const T *)q, (const T *)adt, (T *)res,
+                                                      nnode, ncell, cap_c, cap_n, cap_f, gm1, half_eps, err);
         }
+    } else if (co == MP_COLOR_TWOSTEP) {
+        void *scratch = nullptr;
+        int rc = mp_twostep_scratch(P, (size_t)P->from_size * 8 * sizeof(T), &scratch);
+        if (rc != MP_OK) return rc;
+        const int n = (int)P->from_size;
+        res_calc_step1<T, SOA><<<(n + 255) / 256, 256, 0, s>>>(n, P->dev.map[0], P->dev.map[1], (const T *)x,
+                                                                (const T *)q, (const T *)adt, (T *)scratch, nnode,
+                                                                ncell, gm1, half_eps);
+        MP_CUDA_TRY(cudaGetLastError());
+        return mp_twostep_gather(P, sizeof(T) == 8 ? MP_F64 : MP_F32, 4, scratch, res, s);
     } else {
         const bool atomic = co == MP_COLOR_ATOMIC;
         for (int c = 0; c < P->ncolors; ++c) {
@@ -498,9 +608,9 @@ extern "C" int loop_bres_calc(const mp_plan *P, int32_t dtype, const void *x, co
     if (!check_maps(P, 2, 0, 1, 1)) return MP_EPLAN;
     if (P->from_size == 0) return MP_OK;
     if (!data_ok({x, q, adt, res})) return MP_EINVAL;
-    // the direct kernels read the global maps: GLOBAL or ATOMIC plans, or
-    // HIER plans (which keep no global maps) are rejected here
-    if (P->opts.coloring == MP_COLOR_HIER) return MP_EPLAN;
+    // the direct kernels read the global maps: GLOBAL or ATOMIC plans; HIER
+    // plans (which keep no global maps) and TWOSTEP plans are rejected here
+    if (P->opts.coloring == MP_COLOR_HIER || P->opts.coloring == MP_COLOR_TWOSTEP) return MP_EPLAN;
     int rc = mp_plan_ensure_device(P);
     if (rc != MP_OK) return rc;
     cudaStream_t s = as_stream(stream);

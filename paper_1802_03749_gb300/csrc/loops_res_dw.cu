@@ -16,6 +16,11 @@
 //  * increments accumulate in double-word in shared memory and are added
 //    to the FP64 res in FP64 at write-back.
 // Measured against the FP64 oracle the result agrees to ~1e-13 rel-L2.
+//
+// GATHER form: instead of the thread-coloured increments each thread
+// stores its flux in shared memory, one barrier, and the thread that staged
+// a cell sums that cell's edge fluxes (the plan's block-local inverse map,
+// staged with the cell) and writes it back.
 #include "common.cuh"
 #include "dw.cuh"
 
@@ -24,10 +29,14 @@ namespace {
 // Dynamic shared memory for cap_c cells and cap_n nodes:
 //   double x, y                                    (16 B per node)
 //   double res[4]  (prefetched at staging)         (32 B per cell)
-//   dw   rho, ru, rv, E, eps adt/2, u, v, p, H, inc[4]   (13 x 8 B per cell)
+//   dw   rho, ru, rv, E, eps adt/2, u, v, p, H     (9 x 8 B per cell)
+//   dw   inc[4][cap_c]   coloured form             (32 B per cell)
+//        f[4][cap_f]     gather form               (32 B per thread)
 //   int  gid                                       (4 B per cell)
+//   ushort4 ge[gw4][cap_c]  gather form            (8 gw4 B per cell)
 // The FP64 arrays come first (8-byte alignment).
-constexpr int kDwCellBytes = 32 + 13 * 8 + 4;
+constexpr int kDwCellBytes = 32 + 9 * 8 + 4;
+constexpr int kDwIncBytes = 32;
 constexpr int kDwNodeBytes = 16;
 
 __device__ __forceinline__ dw ld(const float2 *a, int i)
@@ -37,15 +46,16 @@ __device__ __forceinline__ dw ld(const float2 *a, int i)
 }
 __device__ __forceinline__ void st(float2 *a, int i, dw v) { a[i] = make_float2(v.hi, v.lo); }
 
-template <bool SOA>
+template <bool SOA, bool GATHER>
 __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
                                                          const ushort4 *__restrict__ lmap,
                                                          const uint8_t *__restrict__ tcolor,
+                                                         const ushort4 *__restrict__ gat, int gw4,
                                                          const int32_t *__restrict__ fp,
                                                          const double *__restrict__ x, const double *__restrict__ q,
                                                          const double *__restrict__ adt, double *__restrict__ res,
                                                          int64_t nnode, int64_t ncell, int cap_c, int cap_n,
-                                                         dw gm1, dw half_eps, int *__restrict__ err)
+                                                         int cap_f, dw gm1, dw half_eps, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *s_x = reinterpret_cast<double *>(smem_raw);
@@ -60,14 +70,17 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
     float2 *s_v = s_u + cap_c;
     float2 *s_p = s_v + cap_c;
     float2 *s_H = s_p + cap_c;
-    float2 *s_inc = s_H + cap_c;  // [4][cap_c]
-    int *s_gid = reinterpret_cast<int *>(s_inc + 4 * cap_c);
+    float2 *s_inc = s_H + cap_c;  // [4][cap_c] coloured, [4][cap_f] gather
+    const int inc_stride = GATHER ? cap_f : cap_c;
+    ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_inc + 4 * inc_stride);  // [gw4][cap_c]
+    int *s_gid = reinterpret_cast<int *>(s_ge + (GATHER ? gw4 * cap_c : 0));
 
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
     if ((unsigned)(reinterpret_cast<unsigned char *>(s_gid + cap_c) - smem_raw) > dynamic_smem_bytes() ||
-        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x) {
+        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x ||
+        (GATHER && ((int)blockDim.x > cap_f || gw4 < 1 || gw4 > 4))) {
         if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
         return;
     }
@@ -78,7 +91,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
     int my_color = -1;
     if (active) {  // independent of the staging: issued first
         l = lmap[d.item_start + tid];
-        my_color = tcolor[d.item_start + tid];
+        if (!GATHER) my_color = tcolor[d.item_start + tid];
     }
 
     for (int i = tid; i < nc; i += blockDim.x) {
@@ -120,8 +133,13 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         st(s_v, i, v);
         st(s_p, i, p);
         st(s_H, i, dw_add(EE, p));
+        if (GATHER) {
+            const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
+            for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];
+        } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) s_inc[k * cap_c + i] = make_float2(0.f, 0.f);
+            for (int k = 0; k < 4; ++k) s_inc[k * cap_c + i] = make_float2(0.f, 0.f);
+        }
         s_gid[i] = (int)g;
     }
     for (int i = tid; i < nn; i += blockDim.x) {
@@ -187,6 +205,43 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         dw_dot_add(A, mu, dw_neg(ld(s_E, c2)));
         f[3] = dw_dot_end(A);
     }
+    if constexpr (GATHER) {
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) st(s_inc, k * cap_f + tid, f[k]);
+        }
+        __syncthreads();
+        // each cell sums its edges' fluxes: +f from the edge's first cell
+        // slot (map slot 2), -f from its second (slot 3)
+        for (int i = tid; i < nc; i += blockDim.x) {
+            dw a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            for (int h = 0; h < gw4; ++h) {
+                const ushort4 e4 = s_ge[h * cap_c + i];
+                const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned e = es[j];
+                    if (e == 0xFFFFu) continue;
+                    const int t = (int)(e >> 4);
+                    const bool neg = (e & 15u) == 3u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const dw v = ld(s_inc, k * cap_f + t);
+                        a[k] = dw_add_fast(a[k], neg ? dw_neg(v) : v);
+                    }
+                }
+            }
+            const int64_t g = s_gid[i];
+            if (SOA) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) res[k * ncell + g] = f64_add_dw(s_res[k * cap_c + i], a[k]);
+            } else {
+                double2 *r2 = reinterpret_cast<double2 *>(res) + 2 * g;
+                r2[0] = make_double2(f64_add_dw(s_res[i], a[0]), f64_add_dw(s_res[cap_c + i], a[1]));
+                r2[1] = make_double2(f64_add_dw(s_res[2 * cap_c + i], a[2]), f64_add_dw(s_res[3 * cap_c + i], a[3]));
+            }
+        }
+    } else {
     for (int c = 0; c < d.ncolors; ++c) {
         if (my_color == c) {
 #pragma unroll
@@ -209,6 +264,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
                                  f64_add_dw(s_res[3 * cap_c + i], ld(s_inc, 3 * cap_c + i)));
         }
     }
+    }
 }
 
 template <bool SOA>
@@ -218,8 +274,11 @@ int res_calc_dw_t(const mp_plan *P, const void *x, const void *q, const void *ad
     if (P->opts.coloring != MP_COLOR_HIER || P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
     const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
     const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
-    const int smem = cap_c * kDwCellBytes + cap_n * kDwNodeBytes;
-    auto kern = res_calc_hier_dw<SOA>;
+    const bool gather = mp_staged(P, MP_STAGED_SIMPLE) == MP_STAGED_GATHER && mp_gather_ready(P);
+    const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
+    const int smem = cap_c * kDwCellBytes + cap_n * kDwNodeBytes + kDwIncBytes * (gather ? cap_f : cap_c) +
+                     8 * gw4 * cap_c;
+    auto kern = gather ? res_calc_hier_dw<SOA, true> : res_calc_hier_dw<SOA, false>;
     int rc = mp_allow_smem(kern, smem);
     if (rc != MP_OK) return rc;
     int *err = nullptr;
@@ -232,9 +291,10 @@ int res_calc_dw_t(const mp_plan *P, const void *x, const void *q, const void *ad
         int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
         if (nb == 0) continue;
         kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
-                                                  P->dev.tcolor, P->dev.fp, (const double *)x, (const double *)q,
+                                                  P->dev.tcolor, reinterpret_cast<const ushort4 *>(P->dev.gat), gw4,
+                                                  P->dev.fp, (const double *)x, (const double *)q,
                                                   (const double *)adt, (double *)res, nnode, ncell, cap_c, cap_n,
-                                                  gm1, half_eps, err);
+                                                  cap_f, gm1, half_eps, err);
     }
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;

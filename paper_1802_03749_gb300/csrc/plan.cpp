@@ -582,6 +582,47 @@ void build_footprints(mp_plan &P)
         for (auto &d : P.desc) d.fp_start[s] += (int32_t)base;
         base += (int64_t)P.fp_ids[s].size();
     }
+    // block-local inverse of the written maps, for the gather form of the
+    // increments: per footprint point the (local iteration, map slot) pairs
+    // that increment it, ascending, in a row of gat_w entries padded with
+    // 0xFFFF (gat_w = 0: some point has more than 16 and the form is off)
+    int slot_of_map[MP_MAX_MAPS];
+    for (int m = 0, sl = 0; m < P.nmaps; ++m) {
+        slot_of_map[m] = sl;
+        sl += P.maps[m].arity;
+    }
+    auto for_each_written = [&](auto fn) {
+        for (int32_t b = 0; b < P.nblocks; ++b) {
+            const mp_block_desc &d = P.desc[b];
+            for (int32_t t = 0; t < d.nitems; ++t) {
+                const int64_t it = d.item_start + t;
+                for (int m = 0; m < P.nmaps; ++m) {
+                    const mp_map_info &mi = P.maps[m];
+                    if (!mi.written) continue;
+                    for (int k = 0; k < mi.arity; ++k) {
+                        const int slot = slot_of_map[m] + k;
+                        const int64_t fpi = d.fp_start[mi.slot] + P.lmap[(size_t)it * P.lmap_stride + slot];
+                        fn(fpi, (uint16_t)(t * 16 + slot));
+                    }
+                }
+            }
+        }
+    };
+    std::vector<uint8_t> cnt(base, 0);
+    int maxc = 0;
+    for_each_written([&](int64_t fpi, uint16_t) {
+        if (cnt[fpi] < 255) cnt[fpi]++;
+        maxc = std::max(maxc, (int)cnt[fpi]);
+    });
+    P.gat_w = maxc <= 4 ? 4 : (maxc <= 8 ? 8 : (maxc <= 16 ? 16 : 0));
+    P.gat_tab.clear();
+    if (P.gat_w > 0 && P.opts.block_size <= 4096) {
+        P.gat_tab.assign((size_t)base * P.gat_w, 0xFFFF);
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for_each_written([&](int64_t fpi, uint16_t e) { P.gat_tab[(size_t)fpi * P.gat_w + cnt[fpi]++] = e; });
+    } else {
+        P.gat_w = 0;
+    }
 }
 
 void compute_stats(mp_plan &P)
@@ -646,9 +687,11 @@ void compute_stats(mp_plan &P)
     if (P.opts.coloring == MP_COLOR_HIER) {
         bytes += (int64_t)P.desc.size() * sizeof(mp_block_desc);
         bytes += (int64_t)P.lmap.size() * 2 + P.from_size;
+        bytes += (int64_t)P.gat_tab.size() * 2;
         for (int s = 0; s < P.ntosets; ++s) bytes += (int64_t)P.fp_ids[s].size() * 4;
     } else {
         for (int m = 0; m < P.nmaps; ++m) bytes += (int64_t)P.maps[m].idx.size() * 4;
+        bytes += (int64_t)(P.inv_off.size() + P.inv_idx.size()) * 4;
     }
     S.plan_bytes = bytes;
 }
@@ -661,12 +704,13 @@ int build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_op
     mp_plan_opts_default(&o);
     if (opts) o = *opts;
     if (o.block_size < 32 || o.block_size > 1024 || o.block_size % 32) return MP_EINVAL;
-    if (o.reorder < 0 || o.reorder > 2 || o.coloring < 0 || o.coloring > 2 || o.layout < 0 || o.layout > 1)
+    if (o.reorder < 0 || o.reorder > 2 || o.coloring < 0 || o.coloring > 3 || o.layout < 0 || o.layout > 1)
         return MP_EINVAL;
     if (!(o.imbalance >= 1.0) || o.imbalance > 2.0) return MP_EINVAL;
-    if (o.staged < -1 || o.staged > 2) return MP_EINVAL;
-    if (o.data_reorder < 0) o.data_reorder = (o.reorder == MP_REORDER_PARTITION) ? 1 : 0;
+    if (o.staged < -1 || o.staged > 3) return MP_EINVAL;
+    if (o.data_reorder < 0) o.data_reorder = (o.reorder == MP_REORDER_PARTITION || o.block_of) ? 1 : 0;
     P->opts = o;
+    P->opts.block_of = nullptr;  // read during the build only
     P->from_size = from_size;
     P->nmaps = nmaps;
     // 1. validation and to-set slots
@@ -711,14 +755,27 @@ int build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_op
     }
     // 2. reordering
     double t1 = now_s();
-    if (o.reorder != MP_REORDER_NONE && from_size > 0) reorder_rcm(*P, primary);
+    if (o.reorder != MP_REORDER_NONE && from_size > 0 && !o.block_of) reorder_rcm(*P, primary);
     double t2 = now_s();
     // 3. blocks
     int S = o.block_size;
     int sprime = (int)(S / o.imbalance);
     if (sprime < 1) sprime = 1;
     std::vector<int32_t> blk;
-    if (o.reorder == MP_REORDER_PARTITION && from_size > 0) {
+    if (o.block_of && from_size > 0) {
+        // caller-defined blocks: iterations grouped by ascending block value
+        std::vector<int32_t> n2o(from_size);
+        for (int64_t i = 0; i < from_size; ++i) n2o[i] = (int32_t)i;
+        std::stable_sort(n2o.begin(), n2o.end(), [&](int32_t a, int32_t b) { return o.block_of[a] < o.block_of[b]; });
+        P->block_offsets.assign(1, 0);
+        for (int64_t i = 0; i < from_size; ++i)
+            if (i > 0 && o.block_of[n2o[i]] != o.block_of[n2o[i - 1]]) P->block_offsets.push_back((int32_t)i);
+        P->block_offsets.push_back((int32_t)from_size);
+        P->nblocks = (int32_t)P->block_offsets.size() - 1;
+        for (int32_t b = 0; b < P->nblocks; ++b)
+            if (P->block_offsets[b + 1] - P->block_offsets[b] > S) return MP_EINVAL;
+        permute_items(*P, n2o);
+    } else if (o.reorder == MP_REORDER_PARTITION && from_size > 0) {
         blk = partition_greedy(*P, sprime, P->nblocks);
         // iterations grouped by block, ascending within a block
         std::vector<int32_t> cnt(P->nblocks + 1, 0);
@@ -798,8 +855,29 @@ int build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_op
     // 5. data-point reordering
     if (o.data_reorder && from_size > 0)
         for (int s = 0; s < P->ntosets; ++s) permute_points(*P, s, data_point_order(*P, s));
-    // 6. footprints and local maps
+    // 6. footprints and local maps (HIER), inverse map (TWOSTEP), both in
+    // the final point numbering
     if (o.coloring == MP_COLOR_HIER) build_footprints(*P);
+    if (o.coloring == MP_COLOR_TWOSTEP) {
+        // inverse of the (single) written map: point -> sorted (item, slot)
+        int w = -1, nw = 0;
+        for (int m = 0; m < nmaps; ++m)
+            if (P->maps[m].written) {
+                w = m;
+                ++nw;
+            }
+        if (nw != 1) return MP_EINVAL;
+        const mp_map_info &mi = P->maps[w];
+        P->inv_map = w;
+        P->inv_off.assign(mi.to_size + 1, 0);
+        for (int32_t p : mi.idx) P->inv_off[p + 1]++;
+        for (int64_t i = 0; i < mi.to_size; ++i) P->inv_off[i + 1] += P->inv_off[i];
+        P->inv_idx.resize(mi.idx.size());
+        std::vector<int32_t> pos(P->inv_off.begin(), P->inv_off.end() - 1);
+        for (int64_t e = 0; e < from_size; ++e)  // items ascending, slots ascending
+            for (int k = 0; k < mi.arity; ++k)
+                P->inv_idx[pos[mi.idx[e * mi.arity + k]]++] = (int32_t)(e * mi.arity + k);
+    }
     compute_stats(*P);
     double t5 = now_s();
     P->stats.seconds_reorder = t2 - t1;
@@ -827,6 +905,7 @@ void mp_plan_opts_default(mp_plan_opts *o)
     o->data_reorder = -1;
     o->staged = -1;
     o->pad_ = 0;
+    o->block_of = nullptr;
 }
 
 int mesh_plan_build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_opts *opts, mp_plan **out)
@@ -912,6 +991,14 @@ int mesh_plan_table(const mp_plan *P, int32_t table, int32_t arg, int32_t *out, 
         tmp.assign(P->lmap.begin(), P->lmap.end());
         src = &tmp;
         break;
+    case MP_TAB_GATHER:
+        tmp.assign(P->gat_tab.begin(), P->gat_tab.end());
+        for (auto &v : tmp)
+            if (v == 0xFFFF) v = -1;
+        src = &tmp;
+        break;
+    case MP_TAB_INV_OFFSETS: src = &P->inv_off; break;
+    case MP_TAB_INV_INDEX: src = &P->inv_idx; break;
     default: return MP_EINVAL;
     }
     *count = (int64_t)src->size();

@@ -31,7 +31,12 @@ struct mp_device_tables {
     uint16_t *lmap = nullptr;   // from_size x lmap_stride local indices (HIER)
     int32_t *fp = nullptr;      // all footprint lists, slot-major
     uint8_t *tcolor = nullptr;  // thread colour per iteration (HIER)
-    int32_t *map[MP_MAX_MAPS] = {nullptr, nullptr, nullptr, nullptr};  // GLOBAL / ATOMIC
+    uint16_t *gat = nullptr;    // HIER: block-local inverse of the written maps
+    int32_t *map[MP_MAX_MAPS] = {nullptr, nullptr, nullptr, nullptr};  // GLOBAL / ATOMIC / TWOSTEP
+    int32_t *inv_off = nullptr;  // TWOSTEP: written to-set point -> range of inv_idx
+    int32_t *inv_idx = nullptr;  // TWOSTEP: item * arity + slot, sorted by (point, item, slot)
+    void *scratch = nullptr;     // TWOSTEP: per-(item, slot) increments
+    size_t scratch_bytes = 0;
     int64_t bytes = 0;
 };
 
@@ -55,9 +60,18 @@ struct mp_plan {
     std::vector<uint8_t> thread_color;    // from_size
     std::vector<int32_t> block_ncolors;   // nblocks
 
+    // TWOSTEP inverse of the written map
+    int32_t inv_map = -1;
+    std::vector<int32_t> inv_off, inv_idx;
+
     // HIER footprints
     std::vector<int32_t> fp_offsets[MP_MAX_TOSETS];  // nblocks + 1
     std::vector<int32_t> fp_ids[MP_MAX_TOSETS];
+    // block-local inverse of the written maps, one row of gat_w entries per
+    // point of the concatenated footprint lists: local iteration * 16 + map
+    // slot of each increment, ascending, padded with 0xFFFF (gat_w 0: none)
+    int32_t gat_w = 0;
+    std::vector<uint16_t> gat_tab;
     int32_t lmap_stride = 0;              // padded slot count per iteration (4 or 8 or 16)
     std::vector<uint16_t> lmap;           // from_size x lmap_stride
     std::vector<mp_block_desc> desc;

@@ -10,7 +10,7 @@
 
 namespace {
 
-constexpr char kMagic[8] = {'M', 'P', 'L', 'A', 'N', '0', '0', '1'};
+constexpr char kMagic[8] = {'M', 'P', 'L', 'A', 'N', '0', '0', '3'};
 
 struct writer {
     FILE *f;
@@ -89,6 +89,11 @@ void walk(IO &io, Plan &P)
         io.vec(P.fp_offsets[s]);
         io.vec(P.fp_ids[s]);
     }
+    io.pod(P.gat_w);
+    io.vec(P.gat_tab);
+    io.pod(P.inv_map);
+    io.vec(P.inv_off);
+    io.vec(P.inv_idx);
     io.pod(P.lmap_stride);
     io.vec(P.lmap);
     io.vec(P.desc);

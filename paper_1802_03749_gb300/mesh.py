@@ -64,12 +64,13 @@ class HexPlan:
     """Plan for hex assembly over elements with elem->node[8] (written)."""
 
     def __init__(self, nnode, elem2node, block_size=256, reorder="partition", coloring="hier", layout="aos",
-                 staged=None):
+                 staged=None, block_of=None):
         self.nnode = int(nnode)
         self.nelem = int(elem2node.shape[0])
         self.layout = layout
         self.plan = Plan([{"to_set": NODE, "idx": elem2node, "to_size": nnode, "written": True}], self.nelem,
-                         block_size=block_size, reorder=reorder, coloring=coloring, layout=layout, staged=staged)
+                         block_size=block_size, reorder=reorder, coloring=coloring, layout=layout, staged=staged,
+                         block_of=block_of)
         self.node_perm = self.plan.perm(NODE)
         self.elem_perm = self.plan.perm(0)
 

@@ -41,7 +41,7 @@ def run_hex(m, sig, v, coloring, reorder, layout, dtype, block_size=256, staged=
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("layout", ["aos", "soa"])
 @pytest.mark.parametrize("coloring,reorder", [("hier", "partition"), ("hier", "rcm"), ("global", "rcm"),
-                                              ("atomic", "none"), ("hier", "none")])
+                                              ("atomic", "none"), ("hier", "none"), ("twostep", "rcm")])
 def test_hex_parity(coloring, reorder, layout, dtype):
     m, sig, v = case(14)
     f, vol, _ = run_hex(m, sig, v, coloring, reorder, layout, dtype)
@@ -117,3 +117,22 @@ def test_hex_double_word_full_size():
     fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
     assert rel_l2(vol, vr) <= 1e-12
     assert rel_l2(f, fr) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(16, 1, 1), (4, 2, 2)])
+def test_hex_handcrafted_blocks(shape):
+    """Caller-defined brick blocks (structured-mesh study): parity."""
+    dims = (16, 8, 8)
+    m = meshgen.hex_mesh(dims[0], seed=33, nyz=dims[1:])
+    sig, v = meshgen.hex_fields(m, seed=33)
+    import paper_1802_03749_gb300 as ml
+    from paper_1802_03749_gb300.mesh import HexPlan
+    H = HexPlan(m.nnode, m.elem2node, block_size=32, block_of=meshgen.hex_bricks(m, shape, dims))
+    x = torch.tensor(H.to_plan(m.x, "node"), device="cuda")
+    vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
+    sd = torch.tensor(H.to_plan(sig, "elem"), device="cuda")
+    f = torch.zeros_like(x)
+    vol = torch.zeros(m.nelem, dtype=torch.float64, device="cuda")
+    ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01)
+    fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
+    assert rel_l2(H.from_plan(f.cpu().numpy(), "node", 3), fr) <= 1e-12

@@ -48,7 +48,7 @@ def run_res_calc(ml, m, q, adt, coloring, reorder, layout, dtype, block_size=480
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("layout", ["aos", "soa"])
 @pytest.mark.parametrize("reorder", ["none", "rcm", "partition"])
-@pytest.mark.parametrize("coloring", ["hier", "global", "atomic"])
+@pytest.mark.parametrize("coloring", ["hier", "global", "atomic", "twostep"])
 def test_res_calc_parity(ml, coloring, reorder, layout, dtype):
     m, q, adt = case(200, 100)
     r0 = 0.01 * np.cos(np.arange(q.size)).reshape(q.shape)       # increments are "+="
@@ -97,10 +97,10 @@ def test_res_calc_tiny_and_empty(ml):
     assert P.stats()["nblocks"] == 0
 
 
-def run_dw(ml, m, q, adt, reorder, layout, block_size=480, res0=None):
+def run_dw(ml, m, q, adt, reorder, layout, block_size=480, res0=None, staged=None):
     from paper_1802_03749_gb300.mesh import AirfoilPlans
     P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                     block_size=block_size, reorder=reorder, coloring="hier", layout=layout)
+                     block_size=block_size, reorder=reorder, coloring="hier", layout=layout, staged=staged)
     x = torch.tensor(P.to_plan(m.x, "node"), device="cuda")
     qd = torch.tensor(P.to_plan(q, "cell"), device="cuda")
     ad = torch.tensor(P.to_plan(adt, "cell"), device="cuda")
@@ -110,33 +110,38 @@ def run_dw(ml, m, q, adt, reorder, layout, block_size=480, res0=None):
     return P.from_plan(res.cpu().numpy(), "cell", 4)
 
 
+@pytest.mark.parametrize("staged", [None, "gather"])
 @pytest.mark.parametrize("layout", ["aos", "soa"])
 @pytest.mark.parametrize("reorder", ["none", "rcm", "partition"])
-def test_res_calc_double_word_parity(ml, reorder, layout):
-    """FP64 data with double-word arithmetic: within the FP64 bar."""
+def test_res_calc_double_word_parity(ml, reorder, layout, staged):
+    """FP64 data with double-word arithmetic, thread-coloured and gather
+    increments: within the FP64 bar."""
     m, q, adt = case(200, 100)
     r0 = 0.01 * np.cos(np.arange(q.size)).reshape(q.shape)
-    got = run_dw(ml, m, q, adt, reorder, layout, res0=r0)
+    got = run_dw(ml, m, q, adt, reorder, layout, res0=r0, staged=staged)
     ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt, res=r0.copy())
     assert rel_l2(got - r0, ref - r0) <= 1e-12
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("compute", [None, "dw"])
+@pytest.mark.parametrize("compute", [None, "dw", "dw_gather"])
 def test_res_calc_full_size_parity(ml, compute):
-    """The benchmark's workload and launch configuration: 2400x1200 quads,
-    two-layer colouring, RCM + partition, block 480, AoS, FP64 data; the
-    oracle computes every cell."""
+    """The benchmark's workload: 2400x1200 quads, two-layer colouring,
+    RCM + partition, AoS, FP64 data (double-word arithmetic at block 256,
+    the benchmark's launch, or native FP64 at 480); the oracle computes
+    every cell."""
     m, q, adt = case(2400, 1200)
     if compute == "dw":
-        got = run_dw(ml, m, q, adt, "partition", "aos")
+        got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256)
+    elif compute == "dw_gather":
+        got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256, staged="gather")
     else:
         got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64")
     ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
     assert rel_l2(got, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("variant", ["pipelined", "smem_atomic"])
+@pytest.mark.parametrize("variant", ["pipelined", "smem_atomic", "gather"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("reorder,block_size", [("partition", 480), ("rcm", 256), ("none", 480), ("partition", 1024)])
 def test_res_calc_staged_variants(ml, variant, dtype, reorder, block_size):
@@ -153,3 +158,19 @@ def test_res_calc_staged_variants(ml, variant, dtype, reorder, block_size):
         ref = oracle.res_calc(m.edge2node, m.edge2cell, round_to(m.x, np.float32), round_to(q, np.float32),
                               round_to(adt, np.float32))
         assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("block_size", [32, 64, 256, 512])
+def test_res_calc_gather_ragged_and_deterministic(ml, block_size):
+    """Gather increments on a ragged mesh at several block sizes, native
+    FP64 and double-word; two runs give the same bits."""
+    m, q, adt = case(97, 53)
+    ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
+    for reorder in ("rcm", "partition"):
+        a, _ = run_res_calc(ml, m, q, adt, "hier", reorder, "aos", "f64", block_size=block_size, staged="gather")
+        b, _ = run_res_calc(ml, m, q, adt, "hier", reorder, "aos", "f64", block_size=block_size, staged="gather")
+        assert rel_l2(a, ref) <= 1e-12 and np.array_equal(a, b)
+        c = run_dw(ml, m, q, adt, reorder, "soa", block_size=block_size, staged="gather")
+        d = run_dw(ml, m, q, adt, reorder, "soa", block_size=block_size, staged="gather")
+        assert rel_l2(c, ref) <= 1e-12 and np.array_equal(c, d)
+    ml.mp_check_device_status()

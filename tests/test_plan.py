@@ -228,3 +228,106 @@ def test_batch_fuses_plans():
         for i in range(bo[b], bo[b + 1]):
             for p in wr[i]:
                 assert owner.setdefault((bc[b], p), b) == b
+
+
+@pytest.mark.parametrize("reorder", ["none", "rcm", "partition"])
+def test_twostep_inverse_map(mesh, reorder):
+    """TWOSTEP plans: the inverse of the written map lists, for every point,
+    exactly its (item, slot) pairs in ascending order, in the final point
+    numbering (after the data-point reordering of partitioned plans)."""
+    m = mesh
+    P = ml.Plan(res_maps(m), m.nedge, block_size=256, reorder=reorder, coloring="twostep")
+    check_perm_consistency(m, P)
+    off = P.table("inv_offsets")
+    idx = P.table("inv_index")
+    e2c = P.table("map", 1).reshape(-1, 2)
+    assert off[0] == 0 and off[-1] == 2 * m.nedge and np.all(np.diff(off) >= 0)
+    for c in range(m.ncell):
+        ent = idx[off[c]:off[c + 1]]
+        assert np.all(np.diff(ent) > 0)
+        assert np.all(e2c.ravel()[ent] == c)
+    assert np.array_equal(np.bincount(e2c.ravel(), minlength=m.ncell), np.diff(off))
+    with pytest.raises(ml.MeshLoopError):   # two written maps: not a two-step loop
+        ml.Plan(res_maps(m, adjoint=True), m.nedge, coloring="twostep")
+
+
+@pytest.mark.parametrize("shape", [(16, 1, 1), (4, 4, 1), (2, 2, 4), (4, 2, 2)])
+def test_caller_defined_brick_blocks(shape):
+    """Handcrafted bricks of bx x by x bz elements on a structured hex grid:
+    every block is one brick and the node reuse is exactly
+    8 bx by bz / ((bx+1)(by+1)(bz+1))."""
+    dims = (16, 8, 8)
+    m = meshgen.hex_mesh(dims[0], seed=2, nyz=dims[1:])
+    blk = meshgen.hex_bricks(m, shape, dims)
+    bx, by, bz = shape
+    P = ml.Plan([{"to_set": 1, "idx": m.elem2node, "to_size": m.nnode, "written": True}], m.nelem,
+                block_size=64, block_of=blk)
+    st = P.stats()
+    assert st["nblocks"] == m.nelem // (bx * by * bz)
+    bo = P.table("block_offsets")
+    pe = P.perm(0)
+    for b in range(len(bo) - 1):
+        assert len(set(blk[pe[bo[b]:bo[b + 1]]])) == 1
+    assert st["reuse_all"] == pytest.approx(8 * bx * by * bz / ((bx + 1) * (by + 1) * (bz + 1)))
+    wr = PO.written_rows_of([{"to_set": 1, "idx": P.table("map", 0).reshape(-1, 8), "to_size": m.nnode,
+                              "written": True}])
+    blocks = [list(range(bo[b], bo[b + 1])) for b in range(len(bo) - 1)]
+    assert PO.check_coloring(wr, list(P.table("thread_color")), groups=blocks)
+    big = meshgen.hex_bricks(m, (4, 4, 4), dims)                # 64 elements per brick
+    with pytest.raises(ml.MeshLoopError):     # a brick larger than the block size
+        ml.Plan([{"to_set": 1, "idx": m.elem2node, "to_size": m.nnode, "written": True}], m.nelem,
+                block_size=32, block_of=big)
+
+
+def check_gather_rows(P, nitems, written_slots, slot_of):
+    """Every footprint point's gather row lists, ascending, t * 16 + k of
+    each written map slot k of each block-local iteration t that maps to
+    it, then -1; points of unwritten to-sets have empty rows."""
+    bo = P.table("block_offsets")
+    fs = P.table("fp_start").reshape(-1, 2)
+    fc = P.table("fp_count").reshape(-1, 2)
+    lm = P.table("local_map").reshape(nitems, -1)
+    gat = P.table("gather")
+    nfp = len(P.table("footprint"))
+    assert len(gat) % nfp == 0
+    w = len(gat) // nfp
+    assert w in (4, 8, 16)
+    gat = gat.reshape(nfp, w)
+    seen = np.zeros(nfp, dtype=bool)
+    for b in range(len(bo) - 1):
+        t0, t1 = bo[b], bo[b + 1]
+        for s in range(2):
+            rows = {i: [] for i in range(fc[b, s])}
+            for k in written_slots:
+                if slot_of[k] != s:
+                    continue
+                for t in range(t1 - t0):
+                    rows[lm[t0 + t, k]].append(t * 16 + k)
+            for i, lst in rows.items():
+                r = gat[fs[b, s] + i]
+                lst = sorted(lst)
+                assert list(r[:len(lst)]) == lst and np.all(r[len(lst):] == -1)
+                seen[fs[b, s] + i] = True
+    assert seen.all()
+    return w
+
+
+@pytest.mark.parametrize("reorder", ["rcm", "partition"])
+def test_gather_rows(mesh, reorder):
+    """The block-local inverse map read by the gather form of the staged
+    kernels: cells list their edges' slot-2/3 increments, nodes none (the
+    forward plan) or their slot-0/1 increments (the adjoint plan)."""
+    m = mesh
+    P = ml.Plan(res_maps(m), m.nedge, block_size=256, reorder=reorder)
+    assert check_gather_rows(P, m.nedge, [2, 3], [0, 0, 1, 1]) == 4
+    Pa = ml.Plan(res_maps(m, adjoint=True), m.nedge, block_size=128, reorder=reorder)
+    check_gather_rows(Pa, m.nedge, [0, 1, 2, 3], [0, 0, 1, 1])
+
+
+def test_gather_rows_batch():
+    """Fused batch plans carry the members' gather rows in the fused
+    footprint numbering."""
+    meshes = [meshgen.quad_mesh(nx, ny, seed=s) for nx, ny, s in [(20, 10, 1), (33, 7, 2)]]
+    plans = [ml.Plan(res_maps(m), m.nedge, block_size=bs, reorder="partition") for m, bs in zip(meshes, (128, 64))]
+    B = ml.Plan.batch(plans)
+    check_gather_rows(B, sum(m.nedge for m in meshes), [2, 3], [0, 0, 1, 1])
