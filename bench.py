@@ -441,9 +441,10 @@ def main():
     useful = useful_bytes_res_calc(m.ncell, m.nnode, m.nedge, elt)
     hbm_peak, peak_kind = read_peaks()
 
-    def setup(coloring, reorder, layout=args.layout, bs=args.block_size, staged=None):
+    def setup(coloring, reorder, layout=args.layout, bs=args.block_size, staged=None, recolor=-1):
         P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                         block_size=bs, reorder=reorder, coloring=coloring, layout=layout, staged=staged)
+                         block_size=bs, reorder=reorder, coloring=coloring, layout=layout, staged=staged,
+                         recolor=recolor)
         P.res.upload()
         d = {"x": torch.tensor(P.to_plan(m.x, "node"), dtype=tdt, device="cuda"),
              "q": torch.tensor(P.to_plan(q, "cell"), dtype=tdt, device="cuda"),
@@ -508,15 +509,17 @@ def main():
         other = "gather" if args.staged != "gather" else None
         todo = [("two_layer_partition" + ("_dw" if compute else "") + f"_{other or 'colour'}", "hier", "partition",
                  compute, other),
+                ("two_layer_partition" + ("_dw" if compute else "") + "_first_fit_colours", "hier", "partition",
+                 compute, args.staged, 0),
                 ("two_layer_rcm", "hier", "rcm", compute, args.staged), ("global_rcm", "global", "rcm", None, None),
                 ("global_none", "global", "none", None, None), ("atomic_rcm", "atomic", "rcm", None, None),
                 ("atomic_none", "atomic", "none", None, None), ("twostep_rcm", "twostep", "rcm", None, None)]
         if compute == "dw":
             todo.insert(1, ("two_layer_partition_native_f64", "hier", "partition", None, None))
             todo.insert(2, ("two_layer_partition_native_f64_gather", "hier", "partition", None, "gather"))
-        for name, coloring, reorder, comp, stg in todo:
+        for name, coloring, reorder, comp, stg, *rc in todo:
             try:
-                Pv, dv = setup(coloring, reorder, staged=stg)
+                Pv, dv = setup(coloring, reorder, staged=stg, recolor=rc[0] if rc else -1)
             except ml.MeshLoopError as e:
                 variants[name] = {"error": str(e)}
                 continue

@@ -114,7 +114,13 @@ typedef struct {
     int32_t staged;      /* MP_STAGED_* implementation of HIER loops; -1: the loop's
                             default (MP_STAGED_SMEM_ATOMIC for hex assembly, whose 3D
                             blocks need ~10 thread colours; MP_STAGED_SIMPLE otherwise) */
-    int32_t pad_;
+    int32_t recolor;     /* HIER: after the first-fit block colouring, empty the last
+                            colours when they hold few blocks (at most 1/32 of them)
+                            by moving each of their blocks to an earlier colour
+                            whose conflicting blocks (at most two) can themselves
+                            move to a third colour: fewer, fuller launches.
+                            0: off (the first-fit colouring alone), 1: on,
+                            -1: default (on)                                         */
     const int32_t *block_of; /* optional, host, from_size entries: caller-defined
                             blocks (e.g. handcrafted shapes on a structured mesh,
                             Sec. 3.1.6).  Iterations with equal values form one block
@@ -237,7 +243,11 @@ int mesh_plan_load(const char *path, mp_plan **out);
  * HIER (staged two-layer, the product), GLOBAL or ATOMIC.  dtype MP_F64,
  * MP_F32, or MP_F64_DW (HIER plans only; FP64 data, double-word arithmetic).
  * x: [nodes][2], q: [cells][4], adt: [cells], res: [cells][4] (AoS; SoA
- * transposes each).  stream is a cudaStream_t.                          */
+ * transposes each).  stream is a cudaStream_t.
+ * HIER plans run one launch per block colour; every launch after the first
+ * is a programmatic dependent launch (it stages q, adt and x while the
+ * previous colour finishes and reads res after it), unless the environment
+ * variable MESHLOOP_NO_PDL is set.                                        */
 int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                   void *res, double gam, double eps, void *stream);
 

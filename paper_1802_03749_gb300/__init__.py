@@ -60,7 +60,7 @@ class mp_plan_opts(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("reorder", ctypes.c_int32), ("coloring", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("imbalance", ctypes.c_double), ("eps", ctypes.c_double),
                 ("primary_map", ctypes.c_int32), ("data_reorder", ctypes.c_int32), ("staged", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("block_of", ctypes.c_void_p)]
+                ("recolor", ctypes.c_int32), ("block_of", ctypes.c_void_p)]
 
 
 class mp_plan_stats(ctypes.Structure):
@@ -149,7 +149,7 @@ class Plan:
     def __init__(self, maps, from_size: int, block_size: int = 512, reorder: str = "partition",
                  coloring: str = "hier", layout: str = "aos", imbalance: float = 1.001, eps: float = 0.0,
                  primary_map: int = -1, data_reorder: int = -1, staged: str | None = None, block_of=None,
-                 _handle=None):
+                 recolor: int = -1, _handle=None):
         L = lib()
         self._h = ctypes.c_void_p()
         if _handle is not None:
@@ -176,6 +176,7 @@ class Plan:
         o.primary_map = int(primary_map)
         o.data_reorder = int(data_reorder)
         o.staged = STAGED[staged]
+        o.recolor = int(recolor)
         if block_of is not None:
             bo = np.ascontiguousarray(block_of, dtype=np.int32)
             keep.append(bo)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "plan_internal.h"
 
@@ -19,6 +20,41 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 
 // True when p is 16-byte aligned (vector loads of double2 / float4 rows).
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Programmatic dependent launch between the colour launches of one loop.
+// A launch made with overlap = true may start while the previous kernel of
+// the stream is finishing: its CTAs fill the SMs that the previous launch's
+// last CTAs free, and stage everything that launch does not write (plan
+// tables, read-only dats) before mp_pdl_wait(), which returns once the
+// previous grid has completed and its writes are visible.  Every kernel
+// calls mp_pdl_trigger() first: dependents may then launch as soon as all
+// of its CTAs are resident.  Without the launch attribute both are no-ops.
+// The environment variable MESHLOOP_NO_PDL (any value) turns the overlap
+// off for the process (plain stream order everywhere).
+inline bool mp_pdl_enabled()
+{
+    static const bool on = std::getenv("MESHLOOP_NO_PDL") == nullptr;
+    return on;
+}
+__device__ __forceinline__ void mp_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void mp_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t mp_launch(void (*kern)(KArgs...), int grid, int block, int smem, cudaStream_t s, bool overlap,
+                      Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = overlap && mp_pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // Data accessor for a dat of DIM components per point in AoS ([n][DIM]) or
 // SoA ([DIM][n]) layout.

@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     T *s_f = s_xh + 2 * cap_n;
     int *s_gid = reinterpret_cast<int *>(s_f + (INC == kIncGather ? 4 * cap_f : 0));
 
+    mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
@@ -152,7 +153,9 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         s_H[i] = H;
         // res is prefetched here: increments accumulate onto it in shared
         // memory and the write-back is a plain store (blocks of one colour
-        // share no cell, so no other block touches these values meanwhile)
+        // share no cell, so no other block touches these values meanwhile);
+        // the previous colour's launch writes it
+        mp_pdl_wait();
         T r0, r1, r2, r3;
         load_res<T, SOA>(res, ncell, g, r0, r1, r2, r3);
         s_inc[i] = r0;
@@ -506,13 +509,16 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         int *err = nullptr;
         if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
         const int32_t *fp = P->dev.fp;
+        bool overlap = false;  // the first launch follows the caller's work: plain stream order
         for (int c = 0; c < P->ncolors; ++c) {
             int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
             if (nb == 0) continue;
-            kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
-                                                      P->dev.tcolor, reinterpret_cast<const ushort4 *>(P->dev.gat),
-                                                      gw4, fp, (const T *)x, (const T *)q, (const T *)adt, (T *)res,
-                                                      nnode, ncell, cap_c, cap_n, cap_f, gm1, half_eps, err);
+            MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
+                                  reinterpret_cast<const ushort4 *>(P->dev.lmap), P->dev.tcolor,
+                                  reinterpret_cast<const ushort4 *>(P->dev.gat), gw4, fp, (const T *)x,
+                                  (const T *)q, (const T *)adt, (T *)res, nnode, ncell, cap_c, cap_n, cap_f, gm1,
+                                  half_eps, err));
+            overlap = true;
         }
     } else if (co == MP_COLOR_TWOSTEP) {
         void *scratch = nullptr;

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
     ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_inc + 4 * inc_stride);  // [gw4][cap_c]
     int *s_gid = reinterpret_cast<int *>(s_ge + (GATHER ? gw4 * cap_c : 0));
 
+    mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
             ru = q[ncell + g];
             rv = q[2 * ncell + g];
             E = q[3 * ncell + g];
+            mp_pdl_wait();  // res: written by the previous colour's launch
 #pragma unroll
             for (int k = 0; k < 4; ++k) s_res[k * cap_c + i] = res[k * ncell + g];
         } else {
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
             ru = a.y;
             rv = b.x;
             E = b.y;
+            mp_pdl_wait();  // res: written by the previous colour's launch
             const double2 *r2 = reinterpret_cast<const double2 *>(res) + 2 * g;
             double2 ra = r2[0], rb = r2[1];
             s_res[i] = ra.x;
@@ -287,16 +290,17 @@ int res_calc_dw_t(const mp_plan *P, const void *x, const void *q, const void *ad
     const double g1 = gam - 1.0, he = 0.5 * eps;
     const float g1h = (float)g1, heh = (float)he;
     const dw gm1{g1h, (float)(g1 - (double)g1h)}, half_eps{heh, (float)(he - (double)heh)};
+    bool overlap = false;  // the first launch follows the caller's work: plain stream order
     for (int c = 0; c < P->ncolors; ++c) {
         int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
         if (nb == 0) continue;
-        kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
-                                                  P->dev.tcolor, reinterpret_cast<const ushort4 *>(P->dev.gat), gw4,
-                                                  P->dev.fp, (const double *)x, (const double *)q,
-                                                  (const double *)adt, (double *)res, nnode, ncell, cap_c, cap_n,
-                                                  cap_f, gm1, half_eps, err);
+        MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
+                              reinterpret_cast<const ushort4 *>(P->dev.lmap), P->dev.tcolor,
+                              reinterpret_cast<const ushort4 *>(P->dev.gat), gw4, P->dev.fp, (const double *)x,
+                              (const double *)q, (const double *)adt, (double *)res, nnode, ncell, cap_c, cap_n,
+                              cap_f, gm1, half_eps, err));
+        overlap = true;
     }
-    MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
 

@@ -420,6 +420,219 @@ void written_points(const mp_plan &P, int64_t it, std::vector<std::pair<int, int
     }
 }
 
+// Dissolves the blocks of a sparse last block colour (at most nblocks/32)
+// into pieces of earlier colours: each iteration of such a block joins the
+// first colour c < K-1 whose other blocks touch none of its written points
+// (points the block's own pieces took in c do not count); the iterations
+// that chose c form one new block of colour c.  A block with an iteration
+// that fits no colour stays whole, and then the colour stays.  Pieces are
+// subsets of their block, so no piece exceeds the block size.
+void split_last_color(const mp_plan &P, std::vector<int32_t> &color, int32_t &ncolors,
+                      std::vector<std::vector<int32_t>> &pieces, std::vector<int32_t> &piece_color,
+                      std::vector<char> &dissolved)
+{
+    const int32_t nb = P.nblocks;
+    pieces.clear();
+    piece_color.clear();
+    dissolved.assign(nb, 0);
+    if (ncolors < 2 || ncolors > 64) return;
+    const int last = ncolors - 1;
+    std::vector<int32_t> todo;
+    for (int32_t b = 0; b < nb; ++b)
+        if (color[b] == last) todo.push_back(b);
+    if (todo.empty() || (int64_t)todo.size() * 32 > nb) return;
+    // colours of the blocks touching each written point
+    std::vector<uint64_t> mask[MP_MAX_TOSETS];
+    for (int s = 0; s < P.ntosets; ++s) mask[s].assign(P.toset_size[s], 0);
+    std::vector<std::pair<int, int32_t>> pts;
+    for (int32_t b = 0; b < nb; ++b) {
+        if (color[b] == last) continue;
+        pts.clear();
+        for (int32_t it = P.block_offsets[b]; it < P.block_offsets[b + 1]; ++it) written_points(P, it, pts);
+        for (auto &sp : pts) mask[sp.first][sp.second] |= 1ull << color[b];
+    }
+    bool all = true;
+    std::vector<std::pair<int, int32_t>> mine;  // (slot, point) this block took, per colour below
+    std::vector<uint64_t> mine_mask;
+    for (int32_t B : todo) {
+        const int32_t s0 = P.block_offsets[B], s1 = P.block_offsets[B + 1];
+        std::vector<std::vector<int32_t>> part(last);
+        std::vector<std::pair<std::pair<int, int32_t>, uint64_t>> took;  // point -> colours B took it in
+        auto took_in = [&](const std::pair<int, int32_t> &sp) -> uint64_t {
+            for (auto &t : took)
+                if (t.first == sp) return t.second;
+            return 0;
+        };
+        bool ok = true;
+        for (int32_t it = s0; it < s1 && ok; ++it) {
+            pts.clear();
+            written_points(P, it, pts);
+            int chosen = -1;
+            for (int c = 0; c < last && chosen < 0; ++c) {
+                bool fits = true;
+                for (auto &sp : pts)
+                    if ((mask[sp.first][sp.second] >> c & 1) && !(took_in(sp) >> c & 1)) fits = false;
+                if (fits) chosen = c;
+            }
+            if (chosen < 0) {
+                ok = false;
+                break;
+            }
+            part[chosen].push_back(it);
+            for (auto &sp : pts) {
+                bool found = false;
+                for (auto &t : took)
+                    if (t.first == sp) {
+                        t.second |= 1ull << chosen;
+                        found = true;
+                    }
+                if (!found) took.push_back({sp, 1ull << chosen});
+            }
+        }
+        if (!ok) {
+            all = false;
+            continue;
+        }
+        // the pieces now own their points in their colours
+        for (auto &t : took) mask[t.first.first][t.first.second] |= t.second;
+        dissolved[B] = 1;
+        for (int c = 0; c < last; ++c)
+            if (!part[c].empty()) {
+                pieces.push_back(std::move(part[c]));
+                piece_color.push_back(c);
+            }
+    }
+    if (all) ncolors = last;
+}
+
+// Empties sparse trailing block colours after first fit.  First fit on a
+// partitioned mesh typically leaves a last colour or two with a handful of
+// blocks, each a launch of its own.  For every block B of the last colour K-1
+// (while it holds at most nblocks/32 blocks), in order:
+//  1. an earlier colour c whose blocks conflicting with B (sharing a written
+//     point) are at most two and can each move to a colour c' < K-1,
+//     c' != c, free of conflicts: apply the moves, B takes c;
+//  2. otherwise a Kempe-chain interchange: for colours c != c2 below K-1,
+//     the connected set of c- and c2-coloured blocks reachable from B's
+//     c-neighbours; if it holds none of B's c2-neighbours, swapping c and c2
+//     inside it frees c for B (the swap keeps the colouring valid).
+// Stops at the first colour that cannot be emptied completely (the blocks
+// already moved stay moved: still a valid colouring).  Deterministic.
+void reduce_sparse_colors(const mp_plan &P, std::vector<int32_t> &color, int32_t &ncolors)
+{
+    const int32_t nb = P.nblocks;
+    if (nb < 2 || ncolors < 2) return;
+    // block adjacency through shared written points
+    std::vector<int32_t> off[MP_MAX_TOSETS], lst[MP_MAX_TOSETS];
+    std::vector<std::pair<int, int32_t>> pts;
+    std::vector<std::vector<std::pair<int, int32_t>>> bpts(nb);
+    for (int s = 0; s < P.ntosets; ++s) off[s].assign(P.toset_size[s] + 1, 0);
+    for (int32_t b = 0; b < nb; ++b) {
+        pts.clear();
+        for (int32_t it = P.block_offsets[b]; it < P.block_offsets[b + 1]; ++it) written_points(P, it, pts);
+        std::sort(pts.begin(), pts.end());
+        pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+        for (auto &sp : pts) off[sp.first][sp.second + 1]++;
+        bpts[b] = pts;
+    }
+    for (int s = 0; s < P.ntosets; ++s) {
+        for (int64_t i = 0; i < P.toset_size[s]; ++i) off[s][i + 1] += off[s][i];
+        lst[s].assign(off[s].back(), 0);
+    }
+    {
+        std::vector<int32_t> pos[MP_MAX_TOSETS];
+        for (int s = 0; s < P.ntosets; ++s) pos[s].assign(off[s].begin(), off[s].end() - 1);
+        for (int32_t b = 0; b < nb; ++b)
+            for (auto &sp : bpts[b]) lst[sp.first][pos[sp.first][sp.second]++] = b;
+    }
+    std::vector<std::vector<int32_t>> adj(nb);
+    for (int32_t b = 0; b < nb; ++b) {
+        std::vector<int32_t> &a = adj[b];
+        for (auto &sp : bpts[b])
+            for (int32_t j = off[sp.first][sp.second]; j < off[sp.first][sp.second + 1]; ++j)
+                if (lst[sp.first][j] != b) a.push_back(lst[sp.first][j]);
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+    auto free_in = [&](int32_t b, int c) {
+        for (int32_t n : adj[b])
+            if (color[n] == c) return false;
+        return true;
+    };
+    std::vector<int32_t> chain, mark(nb, 0);
+    int32_t stamp = 1;
+    while (ncolors > 1) {
+        const int last = ncolors - 1;
+        std::vector<int32_t> todo;
+        for (int32_t b = 0; b < nb; ++b)
+            if (color[b] == last) todo.push_back(b);
+        if ((int64_t)todo.size() * 32 > nb) return;
+        // a few sweeps: a later placement can open a way for an earlier block
+        for (int sweep = 0; sweep < 4 && !todo.empty(); ++sweep) {
+        std::vector<int32_t> left;
+        for (int32_t B : todo) {
+            bool placed = false;
+            for (int c = 0; c < last && !placed; ++c) {
+                std::vector<int32_t> conf;
+                for (int32_t n : adj[B])
+                    if (color[n] == c) conf.push_back(n);
+                if (conf.size() > 2) continue;
+                std::vector<std::pair<int32_t, int>> undo;
+                bool ok = true;
+                for (int32_t N : conf) {
+                    int to = -1;
+                    for (int c2 = 0; c2 < last && to < 0; ++c2)
+                        if (c2 != c && free_in(N, c2)) to = c2;
+                    if (to < 0) {
+                        ok = false;
+                        break;
+                    }
+                    undo.emplace_back(N, color[N]);
+                    color[N] = to;
+                }
+                if (ok && free_in(B, c)) {
+                    color[B] = c;
+                    placed = true;
+                } else {
+                    for (auto it = undo.rbegin(); it != undo.rend(); ++it) color[it->first] = it->second;
+                }
+            }
+            for (int c = 0; c < last && !placed; ++c)
+                for (int c2 = 0; c2 < last && !placed; ++c2) {
+                    if (c2 == c) continue;
+                    // the (c, c2) chain from B's c-neighbours
+                    chain.clear();
+                    for (int32_t n : adj[B])
+                        if (color[n] == c && mark[n] != stamp) {
+                            mark[n] = stamp;
+                            chain.push_back(n);
+                        }
+                    bool blocked = false;
+                    for (size_t h = 0; h < chain.size() && !blocked; ++h)
+                        for (int32_t n : adj[chain[h]]) {
+                            if (n == B || (color[n] != c && color[n] != c2) || mark[n] == stamp) continue;
+                            mark[n] = stamp;
+                            chain.push_back(n);
+                        }
+                    for (int32_t n : adj[B])
+                        if (color[n] == c2 && mark[n] == stamp) blocked = true;
+                    ++stamp;
+                    if (blocked || chain.empty()) continue;
+                    for (int32_t n : chain) color[n] = color[n] == c ? c2 : c;
+                    color[B] = c;
+                    placed = true;
+                }
+            if (!placed) left.push_back(B);
+        }
+        const bool progress = left.size() < todo.size();
+        todo.swap(left);
+        if (!progress) break;
+        }
+        if (!todo.empty()) return;
+        ncolors = last;
+    }
+}
+
 // Thread colours inside each block: first fit over the block's iterations
 // in order, on written points (64-bit masks, reset per block).  Then the
 // iterations of each block are stably sorted by colour (Sec. 2.4).
@@ -707,7 +920,7 @@ int build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_op
     if (o.reorder < 0 || o.reorder > 2 || o.coloring < 0 || o.coloring > 3 || o.layout < 0 || o.layout > 1)
         return MP_EINVAL;
     if (!(o.imbalance >= 1.0) || o.imbalance > 2.0) return MP_EINVAL;
-    if (o.staged < -1 || o.staged > 3) return MP_EINVAL;
+    if (o.staged < -1 || o.staged > 3 || o.recolor < -1 || o.recolor > 1) return MP_EINVAL;
     if (o.data_reorder < 0) o.data_reorder = (o.reorder == MP_REORDER_PARTITION || o.block_of) ? 1 : 0;
     P->opts = o;
     P->opts.block_of = nullptr;  // read during the build only
@@ -800,19 +1013,34 @@ int build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_op
                                        for (int32_t it = bo[b]; it < bo[b + 1]; ++it) written_points(*P, it, out);
                                    },
                                    MP_MAX_BLOCK_COLORS, P->ncolors);
-        // blocks stably sorted by colour
-        std::vector<int32_t> border(P->nblocks);
-        for (int32_t b = 0; b < P->nblocks; ++b) border[b] = b;
-        std::stable_sort(border.begin(), border.end(),
-                         [&](int32_t x, int32_t y) { return P->block_color[x] < P->block_color[y]; });
+        std::vector<std::vector<int32_t>> pieces;
+        std::vector<int32_t> piece_color;
+        std::vector<char> dissolved(P->nblocks, 0);
+        if (o.recolor != 0) {
+            reduce_sparse_colors(*P, P->block_color, P->ncolors);
+            split_last_color(*P, P->block_color, P->ncolors, pieces, piece_color, dissolved);
+        }
+        // blocks stably sorted by colour (pieces of dissolved blocks after
+        // the whole blocks of their colour)
+        const int32_t nwhole = P->nblocks, nall = nwhole + (int32_t)pieces.size();
+        auto color_of = [&](int32_t x) { return x < nwhole ? P->block_color[x] : piece_color[x - nwhole]; };
+        std::vector<int32_t> border;
+        for (int32_t b = 0; b < nall; ++b)
+            if (b >= nwhole || !dissolved[b]) border.push_back(b);
+        std::stable_sort(border.begin(), border.end(), [&](int32_t x, int32_t y) { return color_of(x) < color_of(y); });
         std::vector<int32_t> n2o;
         n2o.reserve(from_size);
         std::vector<int32_t> nbo(1, 0), nbc;
         for (int32_t b : border) {
-            for (int32_t it = bo[b]; it < bo[b + 1]; ++it) n2o.push_back(it);
+            if (b < nwhole)
+                for (int32_t it = bo[b]; it < bo[b + 1]; ++it) n2o.push_back(it);
+            else
+                n2o.insert(n2o.end(), pieces[b - nwhole].begin(), pieces[b - nwhole].end());
             nbo.push_back((int32_t)n2o.size());
-            nbc.push_back(P->block_color[b]);
+            nbc.push_back(color_of(b));
         }
+        if ((int64_t)n2o.size() != from_size) throw plan_error{MP_EINVAL};
+        P->nblocks = (int32_t)border.size();
         permute_items(*P, n2o);
         P->block_offsets = nbo;
         P->block_color = nbc;
@@ -904,7 +1132,7 @@ void mp_plan_opts_default(mp_plan_opts *o)
     o->primary_map = -1;
     o->data_reorder = -1;
     o->staged = -1;
-    o->pad_ = 0;
+    o->recolor = -1;
     o->block_of = nullptr;
 }
 

@@ -21,14 +21,15 @@ class AirfoilPlans:
     (cells) over one quad mesh given by its maps (original numbering)."""
 
     def __init__(self, ncell, nnode, edge2node, edge2cell, bedge2node, bedge2cell, cell2node,
-                 block_size=512, reorder="partition", coloring="hier", layout="aos", adjoint=False, staged=None):
+                 block_size=512, reorder="partition", coloring="hier", layout="aos", adjoint=False, staged=None,
+                 recolor=-1):
         self.ncell, self.nnode = int(ncell), int(nnode)
         self.nedge, self.nbedge = int(edge2node.shape[0]), int(bedge2node.shape[0])
         self.layout = layout
         self.res = Plan([{"to_set": NODE, "idx": edge2node, "to_size": nnode, "written": adjoint},
                          {"to_set": CELL, "idx": edge2cell, "to_size": ncell, "written": True}],
                         self.nedge, block_size=block_size, reorder=reorder, coloring=coloring, layout=layout,
-                        staged=staged)
+                        staged=staged, recolor=recolor)
         self.cell_perm = self.res.perm(CELL)      # new_to_old
         self.node_perm = self.res.perm(NODE)
         self.edge_perm = self.res.perm(0)
@@ -64,13 +65,13 @@ class HexPlan:
     """Plan for hex assembly over elements with elem->node[8] (written)."""
 
     def __init__(self, nnode, elem2node, block_size=256, reorder="partition", coloring="hier", layout="aos",
-                 staged=None, block_of=None):
+                 staged=None, block_of=None, recolor=-1):
         self.nnode = int(nnode)
         self.nelem = int(elem2node.shape[0])
         self.layout = layout
         self.plan = Plan([{"to_set": NODE, "idx": elem2node, "to_size": nnode, "written": True}], self.nelem,
                          block_size=block_size, reorder=reorder, coloring=coloring, layout=layout, staged=staged,
-                         block_of=block_of)
+                         block_of=block_of, recolor=recolor)
         self.node_perm = self.plan.perm(NODE)
         self.elem_perm = self.plan.perm(0)
 

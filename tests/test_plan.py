@@ -44,8 +44,10 @@ def check_perm_consistency(m, P):
 @pytest.mark.parametrize("reorder", ["none", "rcm", "partition"])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_hier_plan_matches_oracle(mesh, reorder, adjoint):
+    """The paper's colouring steps alone (no sparse-colour elimination)
+    against the Python first-fit oracle."""
     m = mesh
-    P = ml.Plan(res_maps(m, adjoint), m.nedge, block_size=256, reorder=reorder, coloring="hier")
+    P = ml.Plan(res_maps(m, adjoint), m.nedge, block_size=256, reorder=reorder, coloring="hier", recolor=0)
     check_perm_consistency(m, P)
     st = P.stats()
     bo = P.table("block_offsets")
@@ -331,3 +333,46 @@ def test_gather_rows_batch():
     plans = [ml.Plan(res_maps(m), m.nedge, block_size=bs, reorder="partition") for m, bs in zip(meshes, (128, 64))]
     B = ml.Plan.batch(plans)
     check_gather_rows(B, sum(m.nedge for m in meshes), [2, 3], [0, 0, 1, 1])
+
+
+def block_coloring_valid(P, wrows):
+    bo = P.table("block_offsets")
+    bc = P.table("block_color")
+    owner = {}
+    for b in range(len(bo) - 1):
+        for i in range(bo[b], bo[b + 1]):
+            for p in wrows[i]:
+                if owner.setdefault((bc[b], p), b) != b:
+                    return False
+    return True
+
+
+@pytest.mark.parametrize("nx,ny,bs", [(200, 100, 64), (200, 100, 256), (600, 300, 480), (97, 53, 32)])
+def test_sparse_colors_eliminated(nx, ny, bs):
+    """Recolouring after first fit (Kempe interchanges, dissolving the
+    blocks of a sparse last colour into pieces of earlier colours): a valid
+    block colouring with no more colours than first fit, every iteration in
+    exactly one block of at most S' iterations, thread colours valid, and
+    on these meshes one launch fewer."""
+    m = meshgen.quad_mesh(nx, ny, seed=4)
+    P0 = ml.Plan(res_maps(m), m.nedge, block_size=bs, reorder="partition", recolor=0)
+    P1 = ml.Plan(res_maps(m), m.nedge, block_size=bs, reorder="partition", recolor=1)
+    st0, st1 = P0.stats(), P1.stats()
+    assert st1["nblock_colors"] <= st0["nblock_colors"]
+    if (nx, ny, bs) != (97, 53, 32):
+        assert st1["nblock_colors"] <= st0["nblock_colors"] - 1
+    check_perm_consistency(m, P1)
+    wrows = PO.written_rows_of(oracle_maps(m, P1))
+    assert block_coloring_valid(P1, wrows)
+    bo = P1.table("block_offsets")
+    bc = P1.table("block_color")
+    co = P1.table("color_offsets")
+    assert bo[0] == 0 and bo[-1] == m.nedge and np.all(np.diff(bo) >= 1)
+    assert np.diff(bo).max() <= st1["sprime"]
+    assert np.all(np.diff(bc) >= 0) and np.array_equal(co, np.searchsorted(bc, np.arange(bc.max() + 2)))
+    tc = P1.table("thread_color")
+    blocks = [list(range(bo[b], bo[b + 1])) for b in range(len(bo) - 1)]
+    assert PO.check_coloring(wrows, list(tc), groups=blocks)
+    # default options recolour
+    assert ml.Plan(res_maps(m), m.nedge, block_size=bs, reorder="partition").stats()["nblock_colors"] == \
+        st1["nblock_colors"]
