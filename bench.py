@@ -50,6 +50,32 @@ DW_FP32_OPS_PER_OP = 9.7
 DW_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DW_FP32_OPS_PER_OP / 1e12
 
 
+# DRAM bytes (read + write) of one pass of the headline kernel (all block
+# colours: double-word res_calc, gather increments, 2400x1200, block 256,
+# partitioned) from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over the 4 launches of a pass; summary in
+# profiles/res_calc_hier_dw_2400x1200.md).  Valid only for the sources it
+# was measured on: a change to any of them reports null until re-measured.
+HEADLINE_TRAFFIC = {"bytes_per_pass": 417324288, "launches_per_pass": 4,
+                    "config": ("dw", "gather", 256, 2400, 1200, "aos"),
+                    "sha256": "51c466e7b99bce29c8c94b06224e1a6ce0bb3c081aa67bade2b88c5cf639b42d",
+                    "sources": ("loops_res_dw.cu", "dw.cuh", "common.cuh", "plan.cpp", "plan_internal.h")}
+
+
+def headline_traffic(args, head_staged):
+    """Measured DRAM bytes per pass when the kernel sources and the launch
+    configuration are the ones the capture was taken on, else None."""
+    import hashlib
+    T = HEADLINE_TRAFFIC
+    if (args.compute, head_staged, args.block_size, args.nx, args.ny, args.layout) != T["config"]:
+        return None
+    h = hashlib.sha256()
+    for f in T["sources"]:
+        with open(os.path.join(ROOT, "paper_1802_03749_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return T["bytes_per_pass"] if h.hexdigest() == T["sha256"] else None
+
+
 def useful_bytes_res_calc(ncell, nnode, nedge, elt):
     """x (2/node) + q (4/cell) + adt (1/cell) read, res (4/cell) read and
     written (w = 2), two int32 maps of 2 per edge."""
@@ -475,7 +501,10 @@ def main():
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    head_staged = args.staged or ("simple" if args.compute == "f64" else "gather")
+    roof["traffic"] = headline_traffic(args, head_staged)
+    roof["traffic_scope"] = "DRAM bytes per pass (all block-colour launches), as achieved; ncu capture"
+    roof["useful_bytes"] = useful
 
     # ---------------------------------------------------------- e2e (host buffers)
     hx = torch.tensor(P.to_plan(m.x, "node"), dtype=tdt).pin_memory()
@@ -499,15 +528,15 @@ def main():
     del d
 
     # ---------------------------------------------------------- variants
-    head_name = "two_layer_partition" + ("_dw" if compute else "") + (f"_{args.staged}" if args.staged else "")
+    head_name = "two_layer_partition" + ("_dw" if compute else "") + f"_{head_staged}"
     variants = {head_name: {
         "gedges_s": value / world, "ms": ms_step, "useful_gbs": gbs, "block_colors": st["nblock_colors"],
         "thread_colors_mean": st["mean_thread_colors"], "reuse": st["reuse_all"],
         "plan_seconds": st["seconds_total"]}}
     if not args.no_variants:
         ks = max(5, args.steps // 2)
-        other = "gather" if args.staged != "gather" else None
-        todo = [("two_layer_partition" + ("_dw" if compute else "") + f"_{other or 'colour'}", "hier", "partition",
+        other = "gather" if head_staged != "gather" else "simple"
+        todo = [("two_layer_partition" + ("_dw" if compute else "") + f"_{other}", "hier", "partition",
                  compute, other),
                 ("two_layer_partition" + ("_dw" if compute else "") + "_first_fit_colours", "hier", "partition",
                  compute, args.staged, 0),
@@ -549,7 +578,7 @@ def main():
                                    + ("FP32 data" if f32 else "FP64 data")
                                    + (", double-word arithmetic" if compute else "")
                                    + f", two-layer colouring"
-                                   + (f" ({args.staged} increments)" if args.staged else "")
+                                   + f" ({'thread-coloured' if head_staged == 'simple' else head_staged} increments)"
                                    + f", RCM + partition, block {args.block_size}, "
                                    + args.layout.upper(),
                        "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge, "parallelism": f"replicas x{world}",

@@ -113,7 +113,8 @@ typedef struct {
                             -1: default (on with MP_REORDER_PARTITION)              */
     int32_t staged;      /* MP_STAGED_* implementation of HIER loops; -1: the loop's
                             default (MP_STAGED_SMEM_ATOMIC for hex assembly, whose 3D
-                            blocks need ~10 thread colours; MP_STAGED_SIMPLE otherwise) */
+                            blocks need ~10 thread colours; MP_STAGED_GATHER for FP32
+                            and double-word res_calc; MP_STAGED_SIMPLE otherwise)     */
     int32_t recolor;     /* HIER: after the first-fit block colouring, empty the last
                             colours when they hold few blocks (at most 1/32 of them)
                             by moving each of their blocks to an earlier colour

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
     int *s_gc = reinterpret_cast<int *>(s_xi + 2 * cap_n);
     int *s_gn = s_gc + cap_c;
 
+    mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
@@ -101,8 +102,10 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
             int64_t j = SOA ? k * ncell + g : 4 * g + k;
             qq[k] = q[j];
             rb[k] = rbar[j];
-            s_qi[k * cap_c + i] = qbar[j];
         }
+        mp_pdl_wait();  // q_bar, x_bar: written by the previous colour's launch
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s_qi[k * cap_c + i] = qbar[SOA ? k * ncell + g : 4 * g + k];
         T ri = T(1) / qq[0];
         T u = qq[1] * ri, v = qq[2] * ri;
         T p = gm1 * (qq[3] - T(0.5) * (qq[1] * u + qq[2] * v));
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
         int64_t g = fpn[i];
         s_x[i] = SOA ? x[g] : x[2 * g];
         s_x[cap_n + i] = SOA ? x[nnode + g] : x[2 * g + 1];
+        mp_pdl_wait();
         s_xi[i] = SOA ? xbar[g] : xbar[2 * g];
         s_xi[cap_n + i] = SOA ? xbar[nnode + g] : xbar[2 * g + 1];
         s_gn[i] = (int)g;
@@ -265,13 +269,15 @@ int adjoint_t(const mp_plan *P, const void *x, const void *q, const void *adt, c
         if (rc != MP_OK) return rc;
         int *err = nullptr;
         if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
+        bool overlap = false;
         for (int c = 0; c < P->ncolors; ++c) {
             int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
             if (nb == 0) continue;
-            kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
-                                                      P->dev.tcolor, P->dev.fp, (const T *)x, (const T *)q,
-                                                      (const T *)adt, (const T *)rbar, (T *)qbar, (T *)xbar, nnode,
-                                                      ncell, cap_c, cap_n, gm1, half_eps, err);
+            MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
+                                  reinterpret_cast<const ushort4 *>(P->dev.lmap), P->dev.tcolor, P->dev.fp,
+                                  (const T *)x, (const T *)q, (const T *)adt, (const T *)rbar, (T *)qbar, (T *)xbar,
+                                  nnode, ncell, cap_c, cap_n, gm1, half_eps, err));
+            overlap = true;
         }
     } else {
         const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;

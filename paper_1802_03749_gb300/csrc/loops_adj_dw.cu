@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
 #pragma unroll
     for (int k = 0; k < 10; ++k) S[k] = s_cell + k * cap_c;
 
+    mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
@@ -126,9 +127,11 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
             const int64_t j = SOA ? k * ncell + g : 4 * g + k;
             qq[k] = dw_from_double_int(q[j]);
             stw(s_rb, k * cap_c + i, dw_from_double_int(rbar[j]));
-            s_qb[k * cap_c + i] = qbar[j];
             s_qi[k * cap_c + i] = make_float2(0.f, 0.f);
         }
+        mp_pdl_wait();  // q_bar, x_bar: written by the previous colour's launch
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s_qb[k * cap_c + i] = qbar[SOA ? k * ncell + g : 4 * g + k];
         const dw ri = dw_recip(qq[0]);
         const dw u = dw_mul(qq[1], ri), v = dw_mul(qq[2], ri);
         dw_acc A = dw_dot_begin(u, u);
@@ -152,6 +155,7 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         const int64_t g = fpn[i];
         s_x[i] = SOA ? x[g] : x[2 * g];
         s_x[cap_n + i] = SOA ? x[nnode + g] : x[2 * g + 1];
+        mp_pdl_wait();
         s_xb[i] = SOA ? xbar[g] : xbar[2 * g];
         s_xb[cap_n + i] = SOA ? xbar[nnode + g] : xbar[2 * g + 1];
         s_xi[i] = make_float2(0.f, 0.f);
@@ -232,15 +236,16 @@ int adjoint_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt
     const double g1 = gam - 1.0, he = 0.5 * eps;
     const float g1h = (float)g1, heh = (float)he;
     const dw gm1{g1h, (float)(g1 - (double)g1h)}, half_eps{heh, (float)(he - (double)heh)};
+    bool overlap = false;
     for (int c = 0; c < P->ncolors; ++c) {
         const int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
         if (nb == 0) continue;
-        kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const ushort4 *>(P->dev.lmap),
-                                                  P->dev.tcolor, P->dev.fp, (const double *)x, (const double *)q,
-                                                  (const double *)adt, (const double *)rbar, (double *)qbar,
-                                                  (double *)xbar, nnode, ncell, cap_c, cap_n, gm1, half_eps, err);
+        MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
+                              reinterpret_cast<const ushort4 *>(P->dev.lmap), P->dev.tcolor, P->dev.fp,
+                              (const double *)x, (const double *)q, (const double *)adt, (const double *)rbar,
+                              (double *)qbar, (double *)xbar, nnode, ncell, cap_c, cap_n, gm1, half_eps, err));
+        overlap = true;
     }
-    MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
 

@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
     T *s_f = s_v + 3 * cap;                    // [3][cap]
     int *s_gid = reinterpret_cast<int *>(s_f + 3 * cap);
 
+    mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0];
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         s_v[i] = a;
         s_v[cap + i] = b;
         s_v[2 * cap + i] = c;
+        mp_pdl_wait();  // f: written by the previous colour's launch
         load3<T, SOA>(f, nnode, g, a, b, c);
         s_f[i] = a;
         s_f[cap + i] = b;
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(256) hex_direct(int e0, int e1, const int32_t 
                                                   const T *__restrict__ sig, T *__restrict__ f, T *__restrict__ vol,
                                                   int64_t nnode, int64_t nelem, T kappa)
 {
+    mp_pdl_trigger();
     int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= e1) return;
     int nd[8];
@@ -250,6 +253,7 @@ __global__ void __launch_bounds__(256) hex_direct(int e0, int e1, const int32_t 
     load3<T, SOA>(sig, nelem, e, s0, s1, s2);
     hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
     vol[e] = V;
+    if (!ATOMIC) mp_pdl_wait();  // f: read-add-written by the previous colour's launch
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -307,12 +311,15 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
         int *err = nullptr;
         if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
         if (P->opts.block_size > 512) return MP_EINVAL;
+        bool overlap = false;
         for (int c = 0; c < P->ncolors; ++c) {
             int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
             if (nb == 0) continue;
-            kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const uint4 *>(P->dev.lmap),
-                                                      P->dev.tcolor, P->dev.fp, (const T *)x, (const T *)v,
-                                                      (const T *)sig, (T *)f, (T *)vol, nnode, nelem, cap, (T)kappa, err);
+            MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
+                                  reinterpret_cast<const uint4 *>(P->dev.lmap), P->dev.tcolor, P->dev.fp,
+                                  (const T *)x, (const T *)v, (const T *)sig, (T *)f, (T *)vol, nnode, nelem, cap,
+                                  (T)kappa, err));
+            overlap = true;
         }
     } else if (P->opts.coloring == MP_COLOR_TWOSTEP) {
         void *scratch = nullptr;
@@ -325,12 +332,15 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
         return mp_twostep_gather(P, sizeof(T) == 8 ? MP_F64 : MP_F32, 3, scratch, f, s);
     } else {
         const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;
+        bool overlap = false;
         for (int c = 0; c < P->ncolors; ++c) {
             int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
             if (e1 <= e0) continue;
             auto kern = atomic ? hex_direct<T, SOA, true> : hex_direct<T, SOA, false>;
-            kern<<<(e1 - e0 + 255) / 256, 256, 0, s>>>(e0, e1, P->dev.map[0], (const T *)x, (const T *)v,
-                                                       (const T *)sig, (T *)f, (T *)vol, nnode, nelem, (T)kappa);
+            MP_CUDA_TRY(mp_launch(kern, (e1 - e0 + 255) / 256, 256, 0, s, overlap && !atomic, e0, e1, P->dev.map[0],
+                                  (const T *)x, (const T *)v, (const T *)sig, (T *)f, (T *)vol, nnode, nelem,
+                                  (T)kappa));
+            overlap = true;
         }
     }
     MP_CUDA_TRY(cudaGetLastError());

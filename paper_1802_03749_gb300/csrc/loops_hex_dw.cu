@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
     float2 *s_i = s_v + 3 * cap;                           // [3][cap] increments
     int *s_gid = reinterpret_cast<int *>(s_i + 3 * cap);
 
+    mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0];
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
             const int64_t j = SOA ? a * nnode + g : 3 * g + a;
             st2(s_x, a * cap + i, dw_from_double_int(x[j]));
             st2(s_v, a * cap + i, dw_from_double_int(v[j]));
+            mp_pdl_wait();  // f: written by the previous colour's launch
             s_f[a * cap + i] = f[j];
             s_i[a * cap + i] = make_float2(0.f, 0.f);
         }
@@ -223,15 +225,16 @@ int hex_dw_t(const mp_plan *P, const void *x, const void *v, const void *sig, vo
     if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
     const float kh = (float)kappa;
     const dw kap{kh, (float)(kappa - (double)kh)};
+    bool overlap = false;
     for (int c = 0; c < P->ncolors; ++c) {
         const int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
         if (nb == 0) continue;
-        kern<<<nb, P->opts.block_size, smem, s>>>(P->dev.desc, b0, reinterpret_cast<const uint4 *>(P->dev.lmap),
-                                                  P->dev.tcolor, P->dev.fp, (const double *)x, (const double *)v,
-                                                  (const double *)sig, (double *)f, (double *)vol,
-                                                  P->maps[0].to_size, P->from_size, cap, kap, err);
+        MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
+                              reinterpret_cast<const uint4 *>(P->dev.lmap), P->dev.tcolor, P->dev.fp,
+                              (const double *)x, (const double *)v, (const double *)sig, (double *)f, (double *)vol,
+                              P->maps[0].to_size, P->from_size, cap, kap, err));
+        overlap = true;
     }
-    MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
 

@@ -335,6 +335,7 @@ __global__ void __launch_bounds__(256) res_calc_direct(int e0, int e1, const int
                                                        T *__restrict__ res, int64_t nnode, int64_t ncell, T gm1,
                                                        T half_eps)
 {
+    mp_pdl_trigger();
     int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= e1) return;
     int2 nab = reinterpret_cast<const int2 *>(e2n)[e];
@@ -353,6 +354,7 @@ __global__ void __launch_bounds__(256) res_calc_direct(int e0, int e1, const int
     T nyh = T(0.5) * xb - T(0.5) * xa;
     T f[4];
     edge_flux(nxh, nyh, r1, ru1, rv1, E1, u1, v1, p1, H1, a1, r2, ru2, rv2, E2, u2, v2, p2, H2, a2, half_eps, f);
+    if (!ATOMIC) mp_pdl_wait();  // res: read-add-written by the previous colour's launch
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         int64_t j1 = SOA ? k * ncell + cc.x : 4 * (int64_t)cc.x + k;
@@ -496,7 +498,9 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
     if (co == MP_COLOR_HIER) {
         if (P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
         const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
-        const int variant = mp_staged(P, MP_STAGED_SIMPLE);
+        // default increments: gather for FP32 (measured faster on GB300),
+        // thread colours for FP64 (whose extra flux stores cost more there)
+        const int variant = mp_staged(P, sizeof(T) == 4 ? MP_STAGED_GATHER : MP_STAGED_SIMPLE);
         const bool gather = variant == MP_STAGED_GATHER && mp_gather_ready(P);
         const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
         const int smem = cap_c * res_smem_per_cell<T>() + cap_n * res_smem_per_node<T>() + gw4 * cap_c * 8 +
@@ -532,13 +536,16 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         return mp_twostep_gather(P, sizeof(T) == 8 ? MP_F64 : MP_F32, 4, scratch, res, s);
     } else {
         const bool atomic = co == MP_COLOR_ATOMIC;
+        bool overlap = false;  // global colours: the same overlap as the staged launches
         for (int c = 0; c < P->ncolors; ++c) {
             int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
             if (e1 <= e0) continue;
             int grid = (e1 - e0 + 255) / 256;
             auto kern = atomic ? res_calc_direct<T, SOA, true> : res_calc_direct<T, SOA, false>;
-            kern<<<grid, 256, 0, s>>>(e0, e1, P->dev.map[0], P->dev.map[1], (const T *)x, (const T *)q, (const T *)adt,
-                                      (T *)res, nnode, ncell, gm1, half_eps);
+            MP_CUDA_TRY(mp_launch(kern, grid, 256, 0, s, overlap && !atomic, e0, e1, P->dev.map[0], P->dev.map[1],
+                                  (const T *)x, (const T *)q, (const T *)adt, (T *)res, nnode, ncell, gm1,
+                                  half_eps));
+            overlap = true;
         }
     }
     MP_CUDA_TRY(cudaGetLastError());

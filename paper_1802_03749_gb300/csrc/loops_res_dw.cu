@@ -277,7 +277,7 @@ int res_calc_dw_t(const mp_plan *P, const void *x, const void *q, const void *ad
     if (P->opts.coloring != MP_COLOR_HIER || P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
     const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
     const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
-    const bool gather = mp_staged(P, MP_STAGED_SIMPLE) == MP_STAGED_GATHER && mp_gather_ready(P);
+    const bool gather = mp_staged(P, MP_STAGED_GATHER) == MP_STAGED_GATHER && mp_gather_ready(P);
     const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
     const int smem = cap_c * kDwCellBytes + cap_n * kDwNodeBytes + kDwIncBytes * (gather ? cap_f : cap_c) +
                      8 * gw4 * cap_c;

@@ -110,12 +110,12 @@ def run_dw(ml, m, q, adt, reorder, layout, block_size=480, res0=None, staged=Non
     return P.from_plan(res.cpu().numpy(), "cell", 4)
 
 
-@pytest.mark.parametrize("staged", [None, "gather"])
+@pytest.mark.parametrize("staged", [None, "simple"])
 @pytest.mark.parametrize("layout", ["aos", "soa"])
 @pytest.mark.parametrize("reorder", ["none", "rcm", "partition"])
 def test_res_calc_double_word_parity(ml, reorder, layout, staged):
-    """FP64 data with double-word arithmetic, thread-coloured and gather
-    increments: within the FP64 bar."""
+    """FP64 data with double-word arithmetic, gather (the default) and
+    thread-coloured increments: within the FP64 bar."""
     m, q, adt = case(200, 100)
     r0 = 0.01 * np.cos(np.arange(q.size)).reshape(q.shape)
     got = run_dw(ml, m, q, adt, reorder, layout, res0=r0, staged=staged)
@@ -124,7 +124,7 @@ def test_res_calc_double_word_parity(ml, reorder, layout, staged):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("compute", [None, "dw", "dw_gather"])
+@pytest.mark.parametrize("compute", [None, "dw", "dw_colour"])
 def test_res_calc_full_size_parity(ml, compute):
     """The benchmark's workload: 2400x1200 quads, two-layer colouring,
     RCM + partition, AoS, FP64 data (double-word arithmetic at block 256,
@@ -133,15 +133,15 @@ def test_res_calc_full_size_parity(ml, compute):
     m, q, adt = case(2400, 1200)
     if compute == "dw":
         got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256)
-    elif compute == "dw_gather":
-        got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256, staged="gather")
+    elif compute == "dw_colour":
+        got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256, staged="simple")
     else:
         got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64")
     ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
     assert rel_l2(got, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("variant", ["pipelined", "smem_atomic", "gather"])
+@pytest.mark.parametrize("variant", ["pipelined", "smem_atomic", "gather", "simple"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("reorder,block_size", [("partition", 480), ("rcm", 256), ("none", 480), ("partition", 1024)])
 def test_res_calc_staged_variants(ml, variant, dtype, reorder, block_size):
