@@ -24,10 +24,19 @@ Meshes (Sec. 1.1 of the paper: sets, fixed-arity maps and data on sets):
   corner order (-,-,-), (+,-,-), (+,+,-), (-,+,-), (-,-,+), (+,-,+),
   (+,+,+), (-,+,+) in (xi, eta, zeta).
 * ``batch_sizes(...)`` -- quad counts and aspect ratios for a batch of meshes.
+* ``tri_mesh(nx, ny, ...)`` -- 2D triangle mesh (each quad of a jittered
+  nx*ny grid split along a diagonal, alternating), renumbered.  One edge set
+  holds interior and boundary edges: edge->cell[2] with the edge's first
+  cell c1 (the triangle that lists the edge's nodes counter-clockwise) and
+  c2 = the neighbour, or c2 = c1 with flag 1 on the boundary.
+* ``volna_fields`` / ``bookleaf_fields`` -- direct data of the increment-only
+  loops (Sec. 3.1.3 and 3.1.4): per edge 7 floats and 1 integer, per cell 17
+  doubles.
 
 Stream ids (``seed + k``): 1 node jitter, 2 cell permutation, 3 node
 permutation, 4 edge permutation, 5 boundary-edge permutation, 6 state noise,
-7 adjoint seeds, 8 hex fields, 9 batch sizes, 10 free directions for tests.
+7 adjoint seeds, 8 hex fields, 9 batch sizes, 10 free directions for tests,
+11 increment-only loop fields.
 """
 from __future__ import annotations
 
@@ -44,6 +53,7 @@ DEFAULT_SEED = 1802
 
 S_JITTER, S_PERM_CELL, S_PERM_NODE, S_PERM_EDGE, S_PERM_BEDGE = 1, 2, 3, 4, 5
 S_NOISE, S_ADJ, S_HEX, S_BATCH, S_DIR = 6, 7, 8, 9, 10
+S_INC = 11
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -345,3 +355,103 @@ def batch_sizes(count: int = 64, qmin: int = 2000, qmax: int = 400000, amin: flo
     nx = np.maximum(2, np.rint(np.sqrt(q * a))).astype(int)
     ny = np.maximum(2, np.rint(q / nx)).astype(int)
     return list(zip(nx.tolist(), ny.tolist()))
+
+
+# --------------------------------------------------------------------------
+# 2D triangle mesh and the increment-only loops' direct data
+# --------------------------------------------------------------------------
+
+@dataclass
+class TriMesh:
+    nx: int
+    ny: int
+    h: float
+    x: np.ndarray          # [nnode, 2] float64
+    cell2node: np.ndarray  # [ncell, 3] int32, counter-clockwise
+    edge2node: np.ndarray  # [nedge, 2] int32, counter-clockwise in edge2cell[:, 0]
+    edge2cell: np.ndarray  # [nedge, 2] int32; boundary edges repeat the cell
+    eflag: np.ndarray      # [nedge] int32, 1 on boundary edges
+
+    @property
+    def ncell(self) -> int:
+        return self.cell2node.shape[0]
+
+    @property
+    def nnode(self) -> int:
+        return self.x.shape[0]
+
+    @property
+    def nedge(self) -> int:
+        return self.edge2node.shape[0]
+
+
+def tri_mesh(nx: int, ny: int, seed: int = DEFAULT_SEED, jitter: float = 0.2, permute: bool = True) -> TriMesh:
+    """Each quad (i, j) of a jittered nx*ny grid on [0, nx/ny] x [0, 1] is
+    split along the diagonal (i,j)-(i+1,j+1) when i+j is even, else along
+    (i+1,j)-(i,j+1): 2 nx ny triangles, counter-clockwise."""
+    q = quad_mesh(nx, ny, seed=seed, jitter=jitter, permute=False)
+    nnx = nx + 1
+    ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    ci, cj = ci.ravel(), cj.ravel()
+    n00, n10 = cj * nnx + ci, cj * nnx + ci + 1
+    n01, n11 = (cj + 1) * nnx + ci, (cj + 1) * nnx + ci + 1
+    even = (ci + cj) % 2 == 0
+    t1 = np.where(even[:, None], np.stack([n00, n10, n11], 1), np.stack([n00, n10, n01], 1))
+    t2 = np.where(even[:, None], np.stack([n00, n11, n01], 1), np.stack([n10, n11, n01], 1))
+    tri = np.concatenate([t1, t2]).astype(np.int64)
+    ntri = tri.shape[0]
+    # half-edges (a -> b counter-clockwise in triangle t), grouped by node pair
+    a = tri.ravel()
+    b = tri[:, [1, 2, 0]].ravel()
+    t = np.repeat(np.arange(ntri), 3)
+    nnode = q.x.shape[0]
+    key = np.minimum(a, b) * nnode + np.maximum(a, b)
+    order = np.argsort(key, kind="stable")
+    key, a, b, t = key[order], a[order], b[order], t[order]
+    first = np.ones(key.size, dtype=bool)
+    first[1:] = key[1:] != key[:-1]
+    idx = np.flatnonzero(first)
+    cnt = np.diff(np.append(idx, key.size))
+    e2n = np.stack([a[idx], b[idx]], 1)
+    c1 = t[idx]
+    c2 = np.where(cnt == 2, t[np.minimum(idx + 1, key.size - 1)], c1)
+    flag = (cnt == 1).astype(np.int32)
+    x = q.x
+    if permute:
+        pc = permutation(seed, S_PERM_CELL, ntri)
+        pn = permutation(seed, S_PERM_NODE, nnode)
+        pe = permutation(seed, S_PERM_EDGE, e2n.shape[0])
+        ic, inn = _inverse(pc), _inverse(pn)
+        x = x[pn]
+        tri = inn[tri[pc]]
+        e2n = inn[e2n[pe]]
+        c1, c2, flag = ic[c1[pe]], ic[c2[pe]], flag[pe]
+    i32 = lambda v: np.ascontiguousarray(v, dtype=np.int32)
+    return TriMesh(nx, ny, q.h, np.ascontiguousarray(x), i32(tri), i32(e2n), i32(np.stack([c1, c2], 1)), i32(flag))
+
+
+def volna_fields(mesh: TriMesh, seed: int = DEFAULT_SEED):
+    """Direct data of the edge loop: per edge (F0, F1, F2, P, L, nx, ny) with
+    F ~ N(0,1), P ~ U(0.5, 1.5), L the edge length and (nx, ny) the unit normal
+    out of the edge's first cell; the cells' inverse areas.  float64 arrays;
+    the loop runs on their float32 roundings."""
+    xa = mesh.x[mesh.edge2node[:, 0]]
+    xb = mesh.x[mesh.edge2node[:, 1]]
+    d = xb - xa
+    L = np.hypot(d[:, 0], d[:, 1])
+    ne = mesh.nedge
+    F = normal(seed, S_INC, 3 * ne).reshape(ne, 3)
+    P = 0.5 + uniform(seed, S_INC, ne, offset=6 * ne)
+    ed = np.column_stack([F, P, L, d[:, 1] / L, -d[:, 0] / L])
+    p = mesh.x[mesh.cell2node]
+    area = 0.5 * ((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1])
+                  - (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1]))
+    return np.ascontiguousarray(ed), 1.0 / area
+
+
+def bookleaf_fields(ncell: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """Direct data of the cell loop: per cell (rho, m[4], w[4], fx[4], fy[4])
+    with rho ~ U(0.5, 2), m, w ~ U(0, 1), fx, fy ~ N(0, 1); [ncell, 17]."""
+    u = uniform(seed, S_INC, 9 * ncell, offset=1 << 40).reshape(ncell, 9)
+    g = normal(seed, S_INC, 8 * ncell, offset=1 << 41).reshape(ncell, 8)
+    return np.ascontiguousarray(np.column_stack([0.5 + 1.5 * u[:, :1], u[:, 1:], g]))

@@ -76,6 +76,8 @@ def _declare(L):
     L.oracle_hex_force.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _D]
     L.oracle_res_calc_adjoint.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _D, _D]
     L.oracle_res_calc_cstep.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P, _D, _D]
+    L.oracle_space_disc.argtypes = [_I64, _P, _P, _P, _P, _P]
+    L.oracle_getacc.argtypes = [_I64, _P, _P, _P]
 
 
 def _f64(a):
@@ -211,3 +213,23 @@ def res_calc_cstep(edge2node, edge2cell, x, dx, q, dq, adt, h=1e-30, gam=GAMMA, 
     lib().oracle_res_calc_cstep(q.shape[0], e2n.shape[0], pe2n, pe2c, px, pdx, pq, pdq, padt, h,
                                 re.ctypes.data, im.ctypes.data, gam, eps)
     return re, im / h
+
+
+def space_disc(edge2cell, edata, eflag, inv_area, res=None):
+    """Volna-style increment-only edge loop (Sec. 3.1.3); res [ncell, 4] +=."""
+    e2c, pe = _i32(edge2cell)
+    _, pd = _f64(edata)
+    _, pf = _i32(eflag)
+    ia, pa = _f64(inv_area)
+    out = np.zeros((ia.shape[0], 4)) if res is None else np.array(res, dtype=np.float64)
+    lib().oracle_space_disc(e2c.shape[0], pe, pd, pf, pa, out.ctypes.data)
+    return out
+
+
+def getacc(cell2node, cdata, nnode, nd=None):
+    """BookLeaf-style increment-only cell loop (Sec. 3.1.4); nd [nnode, 4] +=."""
+    c2n, pc = _i32(cell2node)
+    _, pd = _f64(cdata)
+    out = np.zeros((nnode, 4)) if nd is None else np.array(nd, dtype=np.float64)
+    lib().oracle_getacc(c2n.shape[0], pc, pd, out.ctypes.data)
+    return out

@@ -24,6 +24,17 @@
  *   hex_force  one-point trilinear hex8 element: stress force -sigma B_i
  *              plus Flanagan-Belytschko hourglass control.
  *   adjoint    reverse-mode derivative of res_calc in q and x (adt fixed).
+ *   space_disc an increment-only edge loop with the access pattern of
+ *              Volna's SpaceDiscretization (Sec. 3.1.3: per edge 7 floats
+ *              and 1 integer read directly, 1 value read and 4 incremented
+ *              on each of 2 cells): the flux through the edge, already
+ *              given per edge, integrated over its length, plus a pressure
+ *              term along the normal, scaled by each cell's inverse area.
+ *   getacc     an increment-only cell loop with the access pattern of
+ *              BookLeaf's getacc_scatter (Sec. 3.1.4: 17 doubles read
+ *              directly per cell, 4 incremented on each of 4 nodes): the
+ *              cell's corner mass, density-weighted corner area and corner
+ *              forces gathered onto the nodes.
  *
  * All arrays are array-of-structures in the caller's numbering:
  * x[node][2], q[cell][4], adt[cell], res[cell][4], hex x/v[node][3],
@@ -382,6 +393,44 @@ void oracle_res_calc_cstep(int64_t ncell, int64_t nedge, const int32_t *edge2nod
             res_im[4 * c1 + k] += cimag(f);
             res_re[4 * c2 + k] -= creal(f);
             res_im[4 * c2 + k] -= cimag(f);
+        }
+    }
+}
+
+/* ------------------------------------------------------ increment-only loops */
+
+/* Volna-style edge loop (Sec. 3.1.3).  Per edge e with cells (c1, c2),
+ * direct data d = (F0, F1, F2, P, L, nx, ny) and flag:
+ *   w = L (F0, F1 + P nx, F2 + P ny, P)
+ *   res[c1] -= inv_area[c1] w;   res[c2] += inv_area[c2] w   unless flag
+ * (a boundary edge lists its one cell twice and has flag 1). */
+void oracle_space_disc(int64_t nedge, const int32_t *edge2cell, const double *edata, const int32_t *eflag,
+                       const double *inv_area, double *res)
+{
+    for (int64_t e = 0; e < nedge; ++e) {
+        const double *d = edata + 7 * e;
+        const double L = d[4];
+        const double w[4] = {L * d[0], L * (d[1] + d[3] * d[5]), L * (d[2] + d[3] * d[6]), L * d[3]};
+        const int32_t c1 = edge2cell[2 * e], c2 = edge2cell[2 * e + 1];
+        for (int k = 0; k < 4; ++k) res[4 * c1 + k] -= inv_area[c1] * w[k];
+        if (!eflag[e])
+            for (int k = 0; k < 4; ++k) res[4 * c2 + k] += inv_area[c2] * w[k];
+    }
+}
+
+/* BookLeaf-style cell loop (Sec. 3.1.4).  Per cell c with nodes n0..n3 and
+ * direct data (rho, m[4], w[4], fx[4], fy[4]):
+ *   nd[n_k] += (m_k, rho w_k, fx_k, fy_k),  k = 0..3 */
+void oracle_getacc(int64_t ncell, const int32_t *cell2node, const double *cdata, double *nd)
+{
+    for (int64_t c = 0; c < ncell; ++c) {
+        const double *d = cdata + 17 * c;
+        for (int k = 0; k < 4; ++k) {
+            double *o = nd + 4 * (int64_t)cell2node[4 * c + k];
+            o[0] += d[1 + k];
+            o[1] += d[0] * d[5 + k];
+            o[2] += d[9 + k];
+            o[3] += d[13 + k];
         }
     }
 }
