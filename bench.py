@@ -273,6 +273,56 @@ def bench_rows(ml, torch, timer, args):
         rows.update(bench_batch(ml, torch, timer, args))
     if "shapes" in want:
         rows.update(bench_shapes(ml, torch, timer, args))
+    if "increment" in want:
+        rows.update(bench_increment(ml, torch, timer, args))
+    return rows
+
+
+def bench_increment(ml, torch, timer, args):
+    """The increment-only loops at the paper's mesh sizes (Sec. 3.1.3 and
+    3.1.4): the Volna-style edge loop in FP32 on 1100x1100 quads split into
+    2.42M triangles (3.63M edges; the paper's mesh has 2.4M triangles and
+    3.59M edges), the BookLeaf-style cell loop in FP64 on 2000x2000 quads
+    (4M cells).  Useful bytes: each dataset once (twice if incremented),
+    maps as int32."""
+    from paper_1802_03749_gb300.mesh import ScatterPlan
+    hbm, _ = read_peaks()
+    rows = {}
+    variants = (("hier", "partition", "gather"), ("hier", "partition", "simple"), ("hier", "rcm", "gather"),
+                ("global", "rcm", None), ("atomic", "rcm", None), ("atomic", "none", None))
+    tm = meshgen.tri_mesh(1100, 1100)
+    ed, ia = meshgen.volna_fields(tm)
+    ub = tm.nedge * (7 * 4 + 4 + 2 * 4) + tm.ncell * (4 + 2 * 16)
+    for coloring, reorder, staged in variants:
+        S = ScatterPlan(tm.ncell, tm.edge2cell, block_size=256, reorder=reorder, coloring=coloring, staged=staged)
+        S.plan.upload()
+        t = lambda a, w: torch.tensor(S.to_plan(a, w), dtype=torch.float32, device="cuda")
+        edd, iad = t(ed, "from"), t(ia, "to")
+        fl = torch.tensor(S.to_plan(tm.eflag, "from"), dtype=torch.int32, device="cuda")
+        res = torch.zeros((tm.ncell, 4), dtype=torch.float32, device="cuda")
+        ms, _ = timer(lambda: ml.loop_space_disc(S.plan, edd, fl, iad, res), 20, 3)
+        st = S.plan.stats()
+        rows[f"space_disc_f32_{coloring}_{reorder}" + (f"_{staged}" if staged else "")] = {
+            "workload": f"Volna-style edge loop, {tm.ncell} triangles, {tm.nedge} edges, FP32", "ms": ms,
+            "gedges_s": tm.nedge / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
+            "block_colors": st["nblock_colors"], "reuse": st["reuse_all"]}
+        del edd, iad, fl, res, S
+    del tm, ed, ia
+    qm = meshgen.quad_mesh(2000, 2000)
+    cd = meshgen.bookleaf_fields(qm.ncell)
+    ub = qm.ncell * (17 * 8 + 4 * 4) + qm.nnode * 2 * 32
+    for coloring, reorder, staged in variants:
+        S = ScatterPlan(qm.nnode, qm.cell2node, block_size=256, reorder=reorder, coloring=coloring, staged=staged)
+        S.plan.upload()
+        cdd = torch.tensor(S.to_plan(cd, "from"), device="cuda")
+        nd = torch.zeros((qm.nnode, 4), dtype=torch.float64, device="cuda")
+        ms, _ = timer(lambda: ml.loop_getacc(S.plan, cdd, nd), 20, 3)
+        st = S.plan.stats()
+        rows[f"getacc_f64_{coloring}_{reorder}" + (f"_{staged}" if staged else "")] = {
+            "workload": f"BookLeaf-style cell loop, {qm.ncell} quads, FP64", "ms": ms,
+            "gcells_s": qm.ncell / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
+            "block_colors": st["nblock_colors"], "reuse": st["reuse_all"]}
+        del cdd, nd, S
     return rows
 
 
@@ -432,8 +482,8 @@ def main():
     ap.add_argument("--compute", default="dw", choices=["dw", "f64", "f32"],
                     help="dw: FP64 data with double-word arithmetic; f64: native FP64; f32: FP32 data")
     ap.add_argument("--no-variants", action="store_true", help="skip the baseline variants")
-    ap.add_argument("--rows", default="hex,adjoint,batch,shapes",
-                    help="other loops to measure (comma list of hex, adjoint, batch, shapes; none for none)")
+    ap.add_argument("--rows", default="hex,adjoint,batch,shapes,increment",
+                    help="other loops to measure (comma list of hex, adjoint, batch, shapes, increment; none for none)")
     ap.add_argument("--no-rows", action="store_true", help="skip the hex / adjoint / batch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--nx", type=int, default=NX, help="quad grid size (profiling runs use smaller meshes)")

@@ -114,7 +114,8 @@ typedef struct {
     int32_t staged;      /* MP_STAGED_* implementation of HIER loops; -1: the loop's
                             default (MP_STAGED_SMEM_ATOMIC for hex assembly, whose 3D
                             blocks need ~10 thread colours; MP_STAGED_GATHER for FP32
-                            and double-word res_calc; MP_STAGED_SIMPLE otherwise)     */
+                            and double-word res_calc and the increment-only loops;
+                            MP_STAGED_SIMPLE otherwise)                               */
     int32_t recolor;     /* HIER: after the first-fit block colouring, empty the last
                             colours when they hold few blocks (at most 1/32 of them)
                             by moving each of their blocks to an earlier colour
@@ -342,6 +343,35 @@ int loop_elem_assemble(const mp_plan *plan, int32_t dtype, const void *x, const 
 int loop_adjoint(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                  const void *res_bar, void *q_bar, void *x_bar, double gam, double eps,
                  void *stream);
+
+/* Increment-only edge loop with the access pattern of Volna's
+ * SpaceDiscretization (Sec. 3.1.3): per edge 7 values and 1 integer read
+ * directly, per cell 1 value read and 4 incremented.  With the edge's
+ * direct data d = (F0, F1, F2, P, L, nx, ny) (flux, pressure, length, unit
+ * normal out of its first cell):
+ *   w = L (F0, F1 + P nx, F2 + P ny, P)
+ *   res[c1] -= inv_area[c1] w;  res[c2] += inv_area[c2] w  unless eflag = 1
+ * (a boundary edge lists its one cell twice and has eflag 1).
+ * Plan: maps {edge->cell (2, written)}; HIER (gather increments by
+ * default, MP_STAGED_SIMPLE for thread colours), GLOBAL or ATOMIC.  dtype MP_F32
+ * (the paper's precision for this loop) or MP_F64.  edata [edges][7] (SoA
+ * [7][edges]), eflag int32 [edges], inv_area [cells], res [cells][4] (SoA
+ * [4][cells]); all device memory in plan numbering, 16-byte aligned.
+ * Errors: MP_EINVAL (dtype, null or misaligned pointer), MP_EPLAN (plan
+ * shape or TWOSTEP colouring), MP_ECUDA.                                  */
+int loop_space_disc(const mp_plan *plan, int32_t dtype, const void *edata, const int32_t *eflag,
+                    const void *inv_area, void *res, void *stream);
+
+/* Increment-only cell loop with the access pattern of BookLeaf's
+ * getacc_scatter (Sec. 3.1.4): per cell 17 values read directly,
+ * (rho, m[4], w[4], fx[4], fy[4]); node k of the cell (cell->node order) gets
+ *   nd[n_k] += (m_k, rho w_k, fx_k, fy_k).
+ * Plan: maps {cell->node (4, written)}; HIER (block size <= 512; gather
+ * increments by default, MP_STAGED_SIMPLE for thread colours), GLOBAL or
+ * ATOMIC.  dtype MP_F64 (the paper's precision) or MP_F32.  cdata
+ * [cells][17] (SoA [17][cells]), nd [nodes][4] (SoA [4][nodes]); device
+ * memory in plan numbering, 16-byte aligned.  Errors as loop_space_disc. */
+int loop_getacc(const mp_plan *plan, int32_t dtype, const void *cdata, void *nd, void *stream);
 
 /* --------------------------------------------------------------- status */
 const char *mp_error_string(int code);

@@ -23,7 +23,7 @@ from . import _build
 
 __all__ = [
     "MeshLoopError", "Plan", "lib", "loop_res_calc", "loop_bres_calc", "loop_adt_calc", "loop_save_soln",
-    "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "mesh_map_renumber", "mp_check_device_status",
+    "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "loop_space_disc", "loop_getacc", "mesh_map_renumber", "mp_check_device_status",
     "REORDER", "COLORING", "LAYOUT", "MP_MAX_BLOCK_COLORS",
 ]
 
@@ -105,6 +105,8 @@ SIGNATURES = {
     "loop_update_noalloc": (_I32, [_I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     "loop_elem_assemble": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _D, _P]),
     "loop_adjoint": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P, _D, _D, _P]),
+    "loop_space_disc": (_I32, [_P, _I32, _P, _P, _P, _P, _P]),
+    "loop_getacc": (_I32, [_P, _I32, _P, _P, _P]),
     "mp_error_string": (ctypes.c_char_p, [_I32]),
     "mp_check_device_status": (_I32, [_P]),
     "mp_version": (ctypes.c_char_p, []),
@@ -370,6 +372,22 @@ def loop_adjoint(plan: Plan, x, q, adt, res_bar, q_bar, x_bar, gam: float = 1.4,
         dt = DTYPE["f64dw"]
     _check(lib().loop_adjoint(plan.handle, dt, _ptr(x), _ptr(q), _ptr(adt), _ptr(res_bar), _ptr(q_bar),
                               _ptr(x_bar), gam, eps, _stream(stream)), "loop_adjoint")
+
+
+def loop_space_disc(plan: Plan, edata, eflag, inv_area, res, stream=None):
+    """Increment-only edge loop (Volna-style, Sec. 3.1.3); res +=."""
+    import torch
+    dt = _dtype_of(edata, inv_area, res)
+    if eflag.dtype != torch.int32 or not eflag.is_cuda or not eflag.is_contiguous():
+        raise MeshLoopError(-1, "eflag must be a contiguous int32 CUDA tensor")
+    _check(lib().loop_space_disc(plan.handle, dt, _ptr(edata), _ptr(eflag), _ptr(inv_area), _ptr(res),
+                                 _stream(stream)), "loop_space_disc")
+
+
+def loop_getacc(plan: Plan, cdata, nd, stream=None):
+    """Increment-only cell loop (BookLeaf-style, Sec. 3.1.4); nd +=."""
+    dt = _dtype_of(cdata, nd)
+    _check(lib().loop_getacc(plan.handle, dt, _ptr(cdata), _ptr(nd), _stream(stream)), "loop_getacc")
 
 
 def mp_check_device_status(stream=None):

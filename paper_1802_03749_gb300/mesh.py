@@ -92,6 +92,41 @@ class HexPlan:
         return out
 
 
+class ScatterPlan:
+    """Plan of an increment-only loop over a from-set with one written map
+    (``loop_space_disc``: edge->cell[2]; ``loop_getacc``: cell->node[4]).
+    ``to_plan``/``from_plan`` move per-item ("from") or per-target ("to")
+    data between the caller's numbering and the plan's numbering and
+    layout."""
+
+    def __init__(self, to_size, from2to, block_size=256, reorder="partition", coloring="hier", layout="aos",
+                 staged=None, recolor=-1):
+        self.to_size = int(to_size)
+        self.from_size = int(from2to.shape[0])
+        self.layout = layout
+        self.plan = Plan([{"to_set": 1, "idx": from2to, "to_size": to_size, "written": True}], self.from_size,
+                         block_size=block_size, reorder=reorder, coloring=coloring, layout=layout, staged=staged,
+                         recolor=recolor)
+        self.from_perm = self.plan.perm(0)
+        self.to_perm = self.plan.perm(1)
+
+    def to_plan(self, a: np.ndarray, which: str) -> np.ndarray:
+        perm = self.from_perm if which == "from" else self.to_perm
+        b = np.asarray(a)[perm]
+        if self.layout == "soa" and b.ndim == 2:
+            b = b.T
+        return np.ascontiguousarray(b)
+
+    def from_plan(self, b: np.ndarray, which: str, dim: int) -> np.ndarray:
+        perm = self.from_perm if which == "from" else self.to_perm
+        b = np.asarray(b)
+        if dim > 1:
+            b = b.reshape(dim, -1).T if self.layout == "soa" else b.reshape(-1, dim)
+        out = np.empty_like(b)
+        out[perm] = b
+        return out
+
+
 class AirfoilStep:
     """One explicit time step of the Airfoil-style solver on the device:
     save_soln, adt_calc, res_calc, bres_calc, update (K = 1 stage per step).
