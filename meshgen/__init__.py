@@ -32,11 +32,16 @@ Meshes (Sec. 1.1 of the paper: sets, fixed-arity maps and data on sets):
 * ``volna_fields`` / ``bookleaf_fields`` -- direct data of the increment-only
   loops (Sec. 3.1.3 and 3.1.4): per edge 7 floats and 1 integer, per cell 17
   doubles.
+* ``hex_faces(mesh, dims)`` / ``aero_cells(mesh)`` -- the interior faces of a
+  structured hex grid (face->cell[2], from the cell on the low side to the
+  cell on the high side, renumbered) with 12 doubles of face geometry each,
+  and 28 doubles of cell data (state, gradients, limiters, centroid) for the
+  face-flux loop (Sec. 3.1.5).
 
 Stream ids (``seed + k``): 1 node jitter, 2 cell permutation, 3 node
 permutation, 4 edge permutation, 5 boundary-edge permutation, 6 state noise,
 7 adjoint seeds, 8 hex fields, 9 batch sizes, 10 free directions for tests,
-11 increment-only loop fields.
+11 increment-only loop fields, 12 face-flux cell data and face permutation.
 """
 from __future__ import annotations
 
@@ -54,6 +59,7 @@ DEFAULT_SEED = 1802
 S_JITTER, S_PERM_CELL, S_PERM_NODE, S_PERM_EDGE, S_PERM_BEDGE = 1, 2, 3, 4, 5
 S_NOISE, S_ADJ, S_HEX, S_BATCH, S_DIR = 6, 7, 8, 9, 10
 S_INC = 11
+S_FACE = 12
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -455,3 +461,66 @@ def bookleaf_fields(ncell: int, seed: int = DEFAULT_SEED) -> np.ndarray:
     u = uniform(seed, S_INC, 9 * ncell, offset=1 << 40).reshape(ncell, 9)
     g = normal(seed, S_INC, 8 * ncell, offset=1 << 41).reshape(ncell, 8)
     return np.ascontiguousarray(np.column_stack([0.5 + 1.5 * u[:, :1], u[:, 1:], g]))
+
+
+# --------------------------------------------------------------------------
+# hex faces and the face-flux loop's data
+# --------------------------------------------------------------------------
+
+# corners of the +x, +y and +z faces of an element (HEX_CORNERS order), listed
+# so that A = (p2 - p0) x (p3 - p1) / 2 points to +x, +y, +z
+_FACE_CORNERS = ((1, 2, 6, 5), (3, 7, 6, 2), (4, 5, 6, 7))
+
+
+def hex_faces(mesh: HexMesh, dims: tuple | None = None, seed: int = DEFAULT_SEED):
+    """Interior faces of the structured grid under ``mesh`` (dims = element
+    counts, default n^3): face->cell[2] (int32; the first cell is on the low
+    side, the area normal points into the second) and per face 12 doubles
+    (A[3] area normal of the bilinear face, xf[3] mean of its corners,
+    nhat[3] = A/|A|, dx[3] = centroid of cell 2 minus centroid of cell 1).
+    Faces are renumbered by a seeded permutation."""
+    nx, ny, nz = dims if dims is not None else (mesh.n, mesh.n, mesh.n)
+    perm = mesh.perms.get("elem", np.arange(mesh.nelem))
+    new_of = _inverse(perm)                      # original element id -> mesh id
+    ek, ej, ei = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ei, ej, ek = ei.ravel(), ej.ravel(), ek.ravel()
+    orig = (ek * ny + ej) * nx + ei
+    c1s, c2s, corners = [], [], []
+    for axis, (lim, step) in enumerate(((nx, 1), (ny, nx), (nz, nx * ny))):
+        pos = (ei, ej, ek)[axis]
+        sel = pos < lim - 1
+        c1 = new_of[orig[sel]]
+        c2 = new_of[orig[sel] + step]
+        c1s.append(c1)
+        c2s.append(c2)
+        corners.append(mesh.elem2node[c1][:, list(_FACE_CORNERS[axis])])
+    c1, c2, fc = np.concatenate(c1s), np.concatenate(c2s), np.concatenate(corners)
+    pf = permutation(seed, S_FACE, c1.size)
+    c1, c2, fc = c1[pf], c2[pf], fc[pf]
+    p = mesh.x[fc]                               # [nf, 4, 3]
+    A = 0.5 * np.cross(p[:, 2] - p[:, 0], p[:, 3] - p[:, 1])
+    xf = p.mean(axis=1)
+    nhat = A / np.linalg.norm(A, axis=1)[:, None]
+    xc = mesh.x[mesh.elem2node].mean(axis=1)
+    dx = xc[c2] - xc[c1]
+    f2c = np.ascontiguousarray(np.stack([c1, c2], 1), dtype=np.int32)
+    return f2c, np.ascontiguousarray(np.column_stack([A, xf, nhat, dx]))
+
+
+def aero_cells(mesh: HexMesh, seed: int = DEFAULT_SEED, gam: float = GAMMA) -> np.ndarray:
+    """Per cell 28 doubles: conserved state Q = (rho, rho u, rho v, rho w, E)
+    with rho ~ U(0.9, 1.1), velocity ~ (0.3, 0.1, 0.05) + U(-0.05, 0.05),
+    p = (1 + 0.1 U(-1, 1)) / gam; gradients of the primitives (rho, u, v, w,
+    p) along x, y, z ~ 0.5 N(0, 1) (index 5 + 3 v + d); limiters ~ U(0.5, 1)
+    (index 20 + v); the cell centroid (index 25..27)."""
+    ne = mesh.nelem
+    u = uniform(seed, S_FACE, 10 * ne, offset=1 << 40).reshape(ne, 10)
+    rho = 0.9 + 0.2 * u[:, 0]
+    vel = np.array([0.3, 0.1, 0.05]) + 0.1 * (u[:, 1:4] - 0.5)
+    p = (1.0 + 0.1 * (2.0 * u[:, 4] - 1.0)) / gam
+    E = p / (gam - 1.0) + 0.5 * rho * (vel ** 2).sum(1)
+    Q = np.column_stack([rho, rho[:, None] * vel, E])
+    G = 0.5 * normal(seed, S_FACE, 15 * ne, offset=1 << 41).reshape(ne, 15)
+    phi = 0.5 + 0.5 * u[:, 5:10]
+    xc = mesh.x[mesh.elem2node].mean(axis=1)
+    return np.ascontiguousarray(np.column_stack([Q, G, phi, xc]))

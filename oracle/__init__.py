@@ -78,6 +78,7 @@ def _declare(L):
     L.oracle_res_calc_cstep.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P, _D, _D]
     L.oracle_space_disc.argtypes = [_I64, _P, _P, _P, _P, _P]
     L.oracle_getacc.argtypes = [_I64, _P, _P, _P]
+    L.oracle_face_flux.argtypes = [_I64, _P, _P, _P, _D, _D, _D, _P]
 
 
 def _f64(a):
@@ -232,4 +233,17 @@ def getacc(cell2node, cdata, nnode, nd=None):
     _, pd = _f64(cdata)
     out = np.zeros((nnode, 4)) if nd is None else np.array(nd, dtype=np.float64)
     lib().oracle_getacc(c2n.shape[0], pc, pd, out.ctypes.data)
+    return out
+
+
+MU, PR = 1e-3, 0.72
+
+
+def face_flux(face2cell, fdata, cdata, res=None, gam=GAMMA, mu=MU, pr=PR):
+    """miniAero-style face flux (Sec. 3.1.5); res [ncell, 5] +=."""
+    f2c, pf = _i32(face2cell)
+    _, pd = _f64(fdata)
+    cd, pc = _f64(cdata)
+    out = np.zeros((cd.shape[0], 5)) if res is None else np.array(res, dtype=np.float64)
+    lib().oracle_face_flux(f2c.shape[0], pf, pd, pc, gam, mu, pr, out.ctypes.data)
     return out

@@ -30,6 +30,12 @@
  *              on each of 2 cells): the flux through the edge, already
  *              given per edge, integrated over its length, plus a pressure
  *              term along the normal, scaled by each cell's inverse area.
+ *   face_flux  a finite-volume face flux with the access pattern of
+ *              miniAero's compute_face_flux (Sec. 3.1.5: per face 12 doubles
+ *              read directly, 28 read and 5 incremented on each of 2 cells):
+ *              limited linear reconstruction to the face, the Rusanov
+ *              (local Lax-Friedrichs) flux of the 3D Euler equations, and a
+ *              Newtonian viscous and heat flux from face gradients.
  *   getacc     an increment-only cell loop with the access pattern of
  *              BookLeaf's getacc_scatter (Sec. 3.1.4: 17 doubles read
  *              directly per cell, 4 incremented on each of 4 nodes): the
@@ -431,6 +437,126 @@ void oracle_getacc(int64_t ncell, const int32_t *cell2node, const double *cdata,
             o[1] += d[0] * d[5 + k];
             o[2] += d[9 + k];
             o[3] += d[13 + k];
+        }
+    }
+}
+
+/* ---------------------------------------------------------------- face flux */
+
+/* Primitives (rho, u, v, w, p) of Q = (rho, rho u, rho v, rho w, E). */
+static void aero_prim(const double *Q, double gam, double *V)
+{
+    V[0] = Q[0];
+    V[1] = Q[1] / Q[0];
+    V[2] = Q[2] / Q[0];
+    V[3] = Q[3] / Q[0];
+    V[4] = (gam - 1.0) * (Q[4] - 0.5 * Q[0] * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]));
+}
+
+/* Conserved state, normal Euler flux, normal velocity and sound speed of the
+ * primitive state V through the unit normal n. */
+static void aero_flux(const double *V, const double *n, double gam, double *Qs, double *F, double *un, double *c)
+{
+    const double rho = V[0], p = V[4];
+    const double E = p / (gam - 1.0) + 0.5 * rho * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
+    *un = V[1] * n[0] + V[2] * n[1] + V[3] * n[2];
+    *c = sqrt(gam * p / rho);
+    Qs[0] = rho;
+    Qs[1] = rho * V[1];
+    Qs[2] = rho * V[2];
+    Qs[3] = rho * V[3];
+    Qs[4] = E;
+    F[0] = rho * *un;
+    F[1] = rho * V[1] * *un + p * n[0];
+    F[2] = rho * V[2] * *un + p * n[1];
+    F[3] = rho * V[3] * *un + p * n[2];
+    F[4] = (E + p) * *un;
+}
+
+/* miniAero-style face flux (Sec. 3.1.5 gives the access pattern; the
+ * arithmetic is this reading).  Face f between cells c1 = face2cell[2f]
+ * and c2 = face2cell[2f+1], face data (A[3], xf[3], nhat[3], dx[3]): A the
+ * area normal from c1 into c2, xf the face centre, nhat = A/|A|, dx the
+ * centroid of c2 minus that of c1.  Cell data (28): Q[5], gradients of the
+ * primitives G[v][d] at 5 + 3 v + d, limiters phi[v] at 20 + v, centroid
+ * xc at 25.
+ *  1. each side: V_face = V_cell + phi (G (xf - xc)) per primitive;
+ *  2. Rusanov: F_inv = |A| ((F(V_1) + F(V_2))/2 - lambda (Q(V_2) - Q(V_1))/2),
+ *     lambda = max over the sides of |u.nhat| + c;
+ *  3. face gradients of u, v, w and T = p/rho: the mean of the two cell
+ *     gradients corrected along dx, g = g_mean + ((phi_2 - phi_1) - g_mean.dx)
+ *     dx / |dx|^2 with the cell-centre values (grad T = (grad p - T grad rho)
+ *     / rho per cell);
+ *  4. viscous flux: tau = mu (grad u + grad u^T) - 2/3 mu (div u) I,
+ *     F_v = (0, tau A, u_f . (tau A) + k grad T . A), u_f the mean of the cell
+ *     velocities, k = mu gam / ((gam - 1) pr);
+ *  5. F = F_inv - F_v;  res[c1] += F, res[c2] -= F  (res [cell][5]). */
+void oracle_face_flux(int64_t nface, const int32_t *face2cell, const double *fdata, const double *cdata, double gam,
+                      double mu, double pr, double *res)
+{
+    for (int64_t f = 0; f < nface; ++f) {
+        const double *fd = fdata + 12 * f;
+        const double *A = fd, *xf = fd + 3, *n = fd + 6, *dx = fd + 9;
+        const int32_t c[2] = {face2cell[2 * f], face2cell[2 * f + 1]};
+        const double area = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+        double Vc[2][5], Qs[2][5], F[2][5], un[2], cs[2];
+        for (int s = 0; s < 2; ++s) {
+            const double *cd = cdata + 28 * (int64_t)c[s];
+            aero_prim(cd, gam, Vc[s]);
+            const double r[3] = {xf[0] - cd[25], xf[1] - cd[26], xf[2] - cd[27]};
+            double Vf[5];
+            for (int v = 0; v < 5; ++v) {
+                const double *g = cd + 5 + 3 * v;
+                Vf[v] = Vc[s][v] + cd[20 + v] * (g[0] * r[0] + g[1] * r[1] + g[2] * r[2]);
+            }
+            aero_flux(Vf, n, gam, Qs[s], F[s], &un[s], &cs[s]);
+        }
+        const double l0 = fabs(un[0]) + cs[0], l1 = fabs(un[1]) + cs[1];
+        const double lam = l0 > l1 ? l0 : l1;
+        double Ft[5];
+        for (int k = 0; k < 5; ++k) Ft[k] = area * (0.5 * (F[0][k] + F[1][k]) - 0.5 * lam * (Qs[1][k] - Qs[0][k]));
+
+        /* face gradients of u, v, w (primitives 1..3) and T */
+        const double *cd1 = cdata + 28 * (int64_t)c[0], *cd2 = cdata + 28 * (int64_t)c[1];
+        const double dd = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+        double gu[3][3], gT[3];
+        for (int a = 0; a < 3; ++a) {
+            const double *g1 = cd1 + 5 + 3 * (1 + a), *g2 = cd2 + 5 + 3 * (1 + a);
+            double gm[3];
+            for (int d = 0; d < 3; ++d) gm[d] = 0.5 * (g1[d] + g2[d]);
+            const double corr = ((Vc[1][1 + a] - Vc[0][1 + a]) - (gm[0] * dx[0] + gm[1] * dx[1] + gm[2] * dx[2])) / dd;
+            for (int d = 0; d < 3; ++d) gu[a][d] = gm[d] + corr * dx[d];
+        }
+        {
+            double T[2], gTc[2][3];
+            const double *cds[2] = {cd1, cd2};
+            for (int s = 0; s < 2; ++s) {
+                T[s] = Vc[s][4] / Vc[s][0];
+                for (int d = 0; d < 3; ++d) gTc[s][d] = (cds[s][5 + 12 + d] - T[s] * cds[s][5 + d]) / Vc[s][0];
+            }
+            double gm[3];
+            for (int d = 0; d < 3; ++d) gm[d] = 0.5 * (gTc[0][d] + gTc[1][d]);
+            const double corr = ((T[1] - T[0]) - (gm[0] * dx[0] + gm[1] * dx[1] + gm[2] * dx[2])) / dd;
+            for (int d = 0; d < 3; ++d) gT[d] = gm[d] + corr * dx[d];
+        }
+        const double div = gu[0][0] + gu[1][1] + gu[2][2];
+        double tA[3];
+        for (int a = 0; a < 3; ++a) {
+            tA[a] = 0.0;
+            for (int b = 0; b < 3; ++b) {
+                const double tau = mu * (gu[a][b] + gu[b][a]) - (a == b ? 2.0 / 3.0 * mu * div : 0.0);
+                tA[a] += tau * A[b];
+            }
+        }
+        const double kappa = mu * gam / ((gam - 1.0) * pr);
+        double uf[3];
+        for (int a = 0; a < 3; ++a) uf[a] = 0.5 * (Vc[0][1 + a] + Vc[1][1 + a]);
+        const double Fv[5] = {0.0, tA[0], tA[1], tA[2],
+                              uf[0] * tA[0] + uf[1] * tA[1] + uf[2] * tA[2] +
+                                  kappa * (gT[0] * A[0] + gT[1] * A[1] + gT[2] * A[2])};
+        for (int k = 0; k < 5; ++k) {
+            res[5 * (int64_t)c[0] + k] += Ft[k] - Fv[k];
+            res[5 * (int64_t)c[1] + k] -= Ft[k] - Fv[k];
         }
     }
 }
