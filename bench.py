@@ -275,6 +275,57 @@ def bench_rows(ml, torch, timer, args):
         rows.update(bench_shapes(ml, torch, timer, args))
     if "increment" in want:
         rows.update(bench_increment(ml, torch, timer, args))
+    if "face" in want:
+        rows.update(bench_face(ml, torch, timer, args))
+    return rows
+
+
+def bench_face(ml, torch, timer, args):
+    """The miniAero-style face flux on the paper's mesh size (Sec. 3.1.5):
+    128^3 hex cells, 6,242,304 interior faces.  FP64 (the paper's
+    precision): the staged forms (28 cell values staged or increments only,
+    thread colours or gather) on one partitioned plan, RCM two-layer, global
+    colours, atomics and the original code's two-step temporary array;
+    FP32 staged and atomics.  Useful bytes: face data and map once, cell data
+    once, res read and written."""
+    from paper_1802_03749_gb300.mesh import ScatterPlan
+    hbm, _ = read_peaks()
+    hm = meshgen.hex_mesh(128)
+    f2c, fd = meshgen.hex_faces(hm)
+    cd = meshgen.aero_cells(hm)
+    nf, nc = f2c.shape[0], hm.nelem
+    rows = {}
+
+    def measure(S, name, dtype):
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        elt = 8 if dtype == "f64" else 4
+        fdd = torch.tensor(S.to_plan(fd, "from"), dtype=tdt, device="cuda")
+        cdd = torch.tensor(S.to_plan(cd, "to"), dtype=tdt, device="cuda")
+        res = torch.zeros((nc, 5), dtype=tdt, device="cuda")
+        ms, _ = timer(lambda: ml.loop_face_flux(S.plan, fdd, cdd, res), 10, 2)
+        ub = nf * (12 * elt + 8) + nc * (28 * elt + 2 * 5 * elt)
+        st = S.plan.stats()
+        rows[f"face_{dtype}_{name}"] = {
+            "workload": f"miniAero-style face flux, {nc} hex cells, {nf} faces, {dtype.upper()}", "ms": ms,
+            "gfaces_s": nf / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
+            "block_colors": st["nblock_colors"], "reuse": st["reuse_all"]}
+        del fdd, cdd, res
+
+    S = ScatterPlan(nc, f2c, block_size=128, reorder="partition", coloring="hier")
+    S.plan.upload()
+    for staged in ("inc_only_gather", "inc_only", "gather", "simple"):
+        S.plan.set_staged(staged)
+        measure(S, f"hier_partition_{staged}", "f64")
+    S.plan.set_staged(None)
+    measure(S, "hier_partition_inc_only_gather", "f32")
+    del S
+    for coloring in ("hier", "global", "atomic", "twostep"):
+        S = ScatterPlan(nc, f2c, block_size=128, reorder="rcm", coloring=coloring)
+        S.plan.upload()
+        measure(S, f"{coloring}_rcm", "f64")
+        if coloring == "atomic":
+            measure(S, f"{coloring}_rcm", "f32")
+        del S
     return rows
 
 
@@ -482,8 +533,9 @@ def main():
     ap.add_argument("--compute", default="dw", choices=["dw", "f64", "f32"],
                     help="dw: FP64 data with double-word arithmetic; f64: native FP64; f32: FP32 data")
     ap.add_argument("--no-variants", action="store_true", help="skip the baseline variants")
-    ap.add_argument("--rows", default="hex,adjoint,batch,shapes,increment",
-                    help="other loops to measure (comma list of hex, adjoint, batch, shapes, increment; none for none)")
+    ap.add_argument("--rows", default="hex,adjoint,batch,shapes,increment,face",
+                    help="other loops to measure (comma list of hex, adjoint, batch, shapes, increment, face; "
+                         "none for none)")
     ap.add_argument("--no-rows", action="store_true", help="skip the hex / adjoint / batch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--nx", type=int, default=NX, help="quad grid size (profiling runs use smaller meshes)")

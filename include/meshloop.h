@@ -228,6 +228,12 @@ int mesh_batch_build(const mp_plan *const *plans, int32_t n, mp_plan **out);
 /* Copy the plan's tables to the current device (synchronous).  Idempotent.*/
 int mesh_plan_upload(mp_plan *plan);
 
+/* Select the staged implementation (MP_STAGED_*, or -1 for each loop's
+ * default) of an existing HIER plan: the tables do not depend on it.  Not
+ * while a loop call on the plan is being issued from another thread.
+ * Errors: MP_EINVAL (null plan or value out of range).                    */
+int mesh_plan_set_staged(mp_plan *plan, int32_t staged);
+
 /* Serialise / restore a plan (reordering is a reusable one-off, Sec. 2.3.2).*/
 int mesh_plan_save(const mp_plan *plan, const char *path);
 int mesh_plan_load(const char *path, mp_plan **out);
@@ -267,7 +273,13 @@ int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void 
  *    order of additions, and so the rounding, is not fixed).  Not for the
  *    double-word res_calc or the adjoint, which run SIMPLE.
  * Block colouring orders the write-back in every variant.                */
-enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2, MP_STAGED_GATHER = 3 };
+enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2, MP_STAGED_GATHER = 3,
+       MP_STAGED_INC_ONLY = 4, MP_STAGED_INC_ONLY_GATHER = 5 };
+/* MP_STAGED_INC_ONLY(_GATHER): shared memory caches only the increments (and
+ * the current values they add to); the loop reads its indirect inputs
+ * through L1/L2 instead of staging them (Sec. 3.1.5: for loops whose
+ * per-point inputs exceed shared memory).  Thread-coloured or gather
+ * increments.  loop_face_flux.                                            */
 /* MP_STAGED_GATHER: no thread colours: each thread stores its iteration's
  * increments in shared memory, one barrier, then every footprint point sums
  * the increments of its iterations in the block (block-local inverse map,
@@ -372,6 +384,28 @@ int loop_space_disc(const mp_plan *plan, int32_t dtype, const void *edata, const
  * [cells][17] (SoA [17][cells]), nd [nodes][4] (SoA [4][nodes]); device
  * memory in plan numbering, 16-byte aligned.  Errors as loop_space_disc. */
 int loop_getacc(const mp_plan *plan, int32_t dtype, const void *cdata, void *nd, void *stream);
+
+/* Face flux with the access pattern of miniAero's compute_face_flux
+ * (Sec. 3.1.5): over interior faces of a hex mesh, 12 values read
+ * directly per face, 28 read and 5 incremented on each of the 2 cells.
+ * Face data (A[3] area normal from c1 into c2, xf[3] face centre, nhat[3] =
+ * A/|A|, dx[3] = xc2 - xc1); cell data (Q[5] = (rho, rho u, rho v, rho w,
+ * E), gradients of the primitives (rho, u, v, w, p) at 5 + 3 v + d, limiters
+ * at 20 + v, centroid at 25).  Per face:
+ *   V_face = V_cell + phi G (xf - xc) on each side; Rusanov flux
+ *   F_inv = |A| ((F(V_1) + F(V_2))/2 - lambda (Q_2 - Q_1)/2);
+ *   Newtonian viscous and heat flux F_v = (0, tau A, u_f.tau A + k grad T.A)
+ *   from the cell gradients corrected along dx (T = p/rho,
+ *   k = mu gam / ((gam - 1) pr));  res[c1] += F_inv - F_v, res[c2] -= it.
+ * Plan: maps {face->cell (2, written)}; HIER (block size <= 256; default
+ * MP_STAGED_INC_ONLY_GATHER; MP_STAGED_SIMPLE / MP_STAGED_GATHER stage the
+ * 28 cell values too), GLOBAL, ATOMIC or TWOSTEP (the original code's
+ * temporary array).  dtype MP_F64 or MP_F32.  fdata [faces][12], cdata
+ * [cells][28], res [cells][5] (SoA: transposed); device memory in plan
+ * numbering, 16-byte aligned.  Errors: MP_EINVAL (dtype, constants, null or
+ * misaligned pointer, block size), MP_EPLAN (plan shape), MP_ECUDA.       */
+int loop_face_flux(const mp_plan *plan, int32_t dtype, const void *fdata, const void *cdata, void *res,
+                   double gam, double mu, double pr, void *stream);
 
 /* --------------------------------------------------------------- status */
 const char *mp_error_string(int code);

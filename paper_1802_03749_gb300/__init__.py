@@ -23,7 +23,7 @@ from . import _build
 
 __all__ = [
     "MeshLoopError", "Plan", "lib", "loop_res_calc", "loop_bres_calc", "loop_adt_calc", "loop_save_soln",
-    "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "loop_space_disc", "loop_getacc", "mesh_map_renumber", "mp_check_device_status",
+    "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "loop_space_disc", "loop_getacc", "loop_face_flux", "mesh_map_renumber", "mp_check_device_status",
     "REORDER", "COLORING", "LAYOUT", "MP_MAX_BLOCK_COLORS",
 ]
 
@@ -35,7 +35,8 @@ MP_MAX_BLOCK_COLORS = 256
 MP_MAX_MAPS = 4
 MP_MAX_TOSETS = 2
 REORDER = {"none": 0, "rcm": 1, "partition": 2}
-STAGED = {None: -1, "pipelined": 0, "simple": 1, "smem_atomic": 2, "gather": 3}
+STAGED = {None: -1, "pipelined": 0, "simple": 1, "smem_atomic": 2, "gather": 3, "inc_only": 4,
+          "inc_only_gather": 5}
 COLORING = {"hier": 0, "global": 1, "atomic": 2, "twostep": 3}
 LAYOUT = {"aos": 0, "soa": 1}
 DTYPE = {"f64": 0, "f32": 1, "f64dw": 2}
@@ -94,6 +95,7 @@ SIGNATURES = {
     "mesh_plan_table": (_I32, [_P, _I32, _I32, _P, _I64, ctypes.POINTER(_I64)]),
     "mesh_map_renumber": (_I32, [_P, _I64, _I32, _P, _P, _I64, _P]),
     "mesh_plan_upload": (_I32, [_P]),
+    "mesh_plan_set_staged": (_I32, [_P, _I32]),
     "mesh_batch_build": (_I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)]),
     "mesh_plan_save": (_I32, [_P, ctypes.c_char_p]),
     "mesh_plan_load": (_I32, [ctypes.c_char_p, ctypes.POINTER(_P)]),
@@ -107,6 +109,7 @@ SIGNATURES = {
     "loop_adjoint": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P, _D, _D, _P]),
     "loop_space_disc": (_I32, [_P, _I32, _P, _P, _P, _P, _P]),
     "loop_getacc": (_I32, [_P, _I32, _P, _P, _P]),
+    "loop_face_flux": (_I32, [_P, _I32, _P, _P, _P, _D, _D, _D, _P]),
     "mp_error_string": (ctypes.c_char_p, [_I32]),
     "mp_check_device_status": (_I32, [_P]),
     "mp_version": (ctypes.c_char_p, []),
@@ -239,6 +242,10 @@ class Plan:
         _check(lib().mesh_plan_table(self._h, t, int(arg), _np_ptr(out), cnt.value, ctypes.byref(cnt)),
                "mesh_plan_table")
         return out
+
+    def set_staged(self, staged: str | None) -> None:
+        """Switch the staged implementation (the tables do not change)."""
+        _check(lib().mesh_plan_set_staged(self.handle, STAGED[staged]), "mesh_plan_set_staged")
 
     def upload(self):
         _check(lib().mesh_plan_upload(self._h), "mesh_plan_upload")
@@ -388,6 +395,14 @@ def loop_getacc(plan: Plan, cdata, nd, stream=None):
     """Increment-only cell loop (BookLeaf-style, Sec. 3.1.4); nd +=."""
     dt = _dtype_of(cdata, nd)
     _check(lib().loop_getacc(plan.handle, dt, _ptr(cdata), _ptr(nd), _stream(stream)), "loop_getacc")
+
+
+def loop_face_flux(plan: Plan, fdata, cdata, res, gam: float = 1.4, mu: float = 1e-3, pr: float = 0.72,
+                   stream=None):
+    """Face flux (miniAero-style, Sec. 3.1.5); res [cells][5] +=."""
+    dt = _dtype_of(fdata, cdata, res)
+    _check(lib().loop_face_flux(plan.handle, dt, _ptr(fdata), _ptr(cdata), _ptr(res), gam, mu, pr,
+                                _stream(stream)), "loop_face_flux")
 
 
 def mp_check_device_status(stream=None):

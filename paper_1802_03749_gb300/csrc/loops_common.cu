@@ -360,6 +360,8 @@ int mp_twostep_gather(const mp_plan *P, int32_t dtype, int dim, const void *scra
         dtype == MP_F64 ? launch_gather<double, 4>(P, scratch, out, s) : launch_gather<float, 4>(P, scratch, out, s);
     else if (dim == 3)
         dtype == MP_F64 ? launch_gather<double, 3>(P, scratch, out, s) : launch_gather<float, 3>(P, scratch, out, s);
+    else if (dim == 5)
+        dtype == MP_F64 ? launch_gather<double, 5>(P, scratch, out, s) : launch_gather<float, 5>(P, scratch, out, s);
     else
         return MP_EINVAL;
     MP_CUDA_TRY(cudaGetLastError());
