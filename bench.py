@@ -313,11 +313,11 @@ def bench_face(ml, torch, timer, args):
 
     S = ScatterPlan(nc, f2c, block_size=128, reorder="partition", coloring="hier")
     S.plan.upload()
-    for staged in ("inc_only_gather", "inc_only", "gather", "simple"):
+    for staged in ("simple", "gather", "inc_only", "inc_only_gather"):
         S.plan.set_staged(staged)
         measure(S, f"hier_partition_{staged}", "f64")
     S.plan.set_staged(None)
-    measure(S, "hier_partition_inc_only_gather", "f32")
+    measure(S, "hier_partition_simple", "f32")
     del S
     for coloring in ("hier", "global", "atomic", "twostep"):
         S = ScatterPlan(nc, f2c, block_size=128, reorder="rcm", coloring=coloring)

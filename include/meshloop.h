@@ -398,9 +398,10 @@ int loop_getacc(const mp_plan *plan, int32_t dtype, const void *cdata, void *nd,
  *   from the cell gradients corrected along dx (T = p/rho,
  *   k = mu gam / ((gam - 1) pr));  res[c1] += F_inv - F_v, res[c2] -= it.
  * Plan: maps {face->cell (2, written)}; HIER (block size <= 256; default
- * MP_STAGED_INC_ONLY_GATHER; MP_STAGED_SIMPLE / MP_STAGED_GATHER stage the
- * 28 cell values too), GLOBAL, ATOMIC or TWOSTEP (the original code's
- * temporary array).  dtype MP_F64 or MP_F32.  fdata [faces][12], cdata
+ * MP_STAGED_SIMPLE: the 28 cell values staged and prepared once per cell,
+ * thread-coloured increments; MP_STAGED_GATHER likewise with gather
+ * increments; MP_STAGED_INC_ONLY[_GATHER] stage the increments only),
+ * GLOBAL, ATOMIC or TWOSTEP (the original code's temporary array).  dtype MP_F64 or MP_F32.  fdata [faces][12], cdata
  * [cells][28], res [cells][5] (SoA: transposed); device memory in plan
  * numbering, 16-byte aligned.  Errors: MP_EINVAL (dtype, constants, null or
  * misaligned pointer, block size), MP_EPLAN (plan shape), MP_ECUDA.       */

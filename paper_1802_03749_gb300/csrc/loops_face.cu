@@ -27,7 +27,7 @@ namespace {
 constexpr int kIncColor = 0, kIncGather = 2;
 constexpr int kCell = 28, kFace = 12;
 
-// cell data accessor: shared-memory SoA [28][stride] or global AoS / SoA
+// cell data accessor: shared-memory SoA [k][stride] or global AoS / SoA
 template <typename T>
 struct cell_at {
     const T *p;
@@ -35,21 +35,53 @@ struct cell_at {
     __device__ __forceinline__ T operator()(int k) const { return p[k * stride]; }
 };
 
+// What a face needs of a cell besides its raw gradients, limiters and
+// centroid: the primitives V = (rho, u, v, w, p), T = p / rho and
+// grad T = (grad p - T grad rho) / rho.  The fully staged kernels compute it
+// once per staged cell (4 divides and ~20 operations a face would
+// otherwise repeat for each of its 2 cells, the FP64 pipe being the bound).
 template <typename T>
-__device__ __forceinline__ void aero_side(const cell_at<T> &c, const T xf[3], const T n[3], T gam, T Vc[5],
-                                          T Qs[5], T F[5], T &lam)
+struct cell_prep {
+    T V[5], Tc, gT[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void prepare_cell(const cell_at<T> &c, T gam, cell_prep<T> &s)
 {
     const T rho = c(0), ri = T(1) / rho;
-    Vc[0] = rho;
-    Vc[1] = c(1) * ri;
-    Vc[2] = c(2) * ri;
-    Vc[3] = c(3) * ri;
-    Vc[4] = (gam - T(1)) * (c(4) - T(0.5) * rho * (Vc[1] * Vc[1] + Vc[2] * Vc[2] + Vc[3] * Vc[3]));
+    s.V[0] = rho;
+    s.V[1] = c(1) * ri;
+    s.V[2] = c(2) * ri;
+    s.V[3] = c(3) * ri;
+    s.V[4] = (gam - T(1)) * (c(4) - T(0.5) * rho * (s.V[1] * s.V[1] + s.V[2] * s.V[2] + s.V[3] * s.V[3]));
+    s.Tc = s.V[4] * ri;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s.gT[d] = (c(17 + d) - s.Tc * c(5 + d)) * ri;
+}
+
+// staged layout of a prepared cell: V at 0..4, raw gradients, limiters and
+// centroid at their own slots 5..27, T at 28, grad T at 29..31
+constexpr int kStaged = 32;
+
+template <typename T>
+__device__ __forceinline__ void load_prep(const cell_at<T> &c, cell_prep<T> &s)
+{
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s.V[v] = c(v);
+    s.Tc = c(28);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s.gT[d] = c(29 + d);
+}
+
+template <typename T>
+__device__ __forceinline__ void aero_side(const cell_at<T> &c, const cell_prep<T> &pc, const T xf[3], const T n[3],
+                                          T gam, T Qs[5], T F[5], T &lam)
+{
     const T r0 = xf[0] - c(25), r1 = xf[1] - c(26), r2 = xf[2] - c(27);
     T V[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v)
-        V[v] = Vc[v] + c(20 + v) * (c(5 + 3 * v) * r0 + c(6 + 3 * v) * r1 + c(7 + 3 * v) * r2);
+        V[v] = pc.V[v] + c(20 + v) * (c(5 + 3 * v) * r0 + c(6 + 3 * v) * r1 + c(7 + 3 * v) * r2);
     const T E = V[4] / (gam - T(1)) + T(0.5) * V[0] * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
     const T un = V[1] * n[0] + V[2] * n[1] + V[3] * n[2];
     lam = fabs(un) + sqrt(gam * V[4] / V[0]);
@@ -67,16 +99,15 @@ __device__ __forceinline__ void aero_side(const cell_at<T> &c, const T xf[3], co
 
 // F = F_inv - F_v of one face
 template <typename T>
-__device__ __forceinline__ void face_flux(const cell_at<T> &c1, const cell_at<T> &c2, const T fd[kFace], T gam, T mu,
-                                          T kappa, T out[5])
+__device__ __forceinline__ void face_flux(const cell_at<T> &c1, const cell_at<T> &c2, const cell_prep<T> &p1,
+                                          const cell_prep<T> &p2, const T fd[kFace], T gam, T mu, T kappa, T out[5])
 {
     const T A[3] = {fd[0], fd[1], fd[2]}, xf[3] = {fd[3], fd[4], fd[5]}, n[3] = {fd[6], fd[7], fd[8]};
     const T dx[3] = {fd[9], fd[10], fd[11]};
-    T V1[5], V2[5];
     {
         T Q1[5], Q2[5], F1[5], F2[5], l1, l2;
-        aero_side(c1, xf, n, gam, V1, Q1, F1, l1);
-        aero_side(c2, xf, n, gam, V2, Q2, F2, l2);
+        aero_side(c1, p1, xf, n, gam, Q1, F1, l1);
+        aero_side(c2, p2, xf, n, gam, Q2, F2, l2);
         const T lam = l1 > l2 ? l1 : l2;
         const T area = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
 #pragma unroll
@@ -89,19 +120,16 @@ __device__ __forceinline__ void face_flux(const cell_at<T> &c1, const cell_at<T>
         T gm[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) gm[d] = T(0.5) * (c1(5 + 3 * (1 + a) + d) + c2(5 + 3 * (1 + a) + d));
-        const T corr = ((V2[1 + a] - V1[1 + a]) - (gm[0] * dx[0] + gm[1] * dx[1] + gm[2] * dx[2])) * idd;
+        const T corr = ((p2.V[1 + a] - p1.V[1 + a]) - (gm[0] * dx[0] + gm[1] * dx[1] + gm[2] * dx[2])) * idd;
 #pragma unroll
         for (int d = 0; d < 3; ++d) gu[a][d] = gm[d] + corr * dx[d];
     }
     T gT[3];
     {
-        const T T1 = V1[4] / V1[0], T2 = V2[4] / V2[0];
-        const T i1 = T(1) / V1[0], i2 = T(1) / V2[0];
         T gm[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            gm[d] = T(0.5) * ((c1(17 + d) - T1 * c1(5 + d)) * i1 + (c2(17 + d) - T2 * c2(5 + d)) * i2);
-        const T corr = ((T2 - T1) - (gm[0] * dx[0] + gm[1] * dx[1] + gm[2] * dx[2])) * idd;
+        for (int d = 0; d < 3; ++d) gm[d] = T(0.5) * (p1.gT[d] + p2.gT[d]);
+        const T corr = ((p2.Tc - p1.Tc) - (gm[0] * dx[0] + gm[1] * dx[1] + gm[2] * dx[2])) * idd;
 #pragma unroll
         for (int d = 0; d < 3; ++d) gT[d] = gm[d] + corr * dx[d];
     }
@@ -116,11 +144,23 @@ __device__ __forceinline__ void face_flux(const cell_at<T> &c1, const cell_at<T>
             tA[a] += tau * A[b];
         }
     }
-    const T uf0 = T(0.5) * (V1[1] + V2[1]), uf1 = T(0.5) * (V1[2] + V2[2]), uf2 = T(0.5) * (V1[3] + V2[3]);
+    const T uf0 = T(0.5) * (p1.V[1] + p2.V[1]), uf1 = T(0.5) * (p1.V[2] + p2.V[2]);
+    const T uf2 = T(0.5) * (p1.V[3] + p2.V[3]);
     out[1] -= tA[0];
     out[2] -= tA[1];
     out[3] -= tA[2];
     out[4] -= uf0 * tA[0] + uf1 * tA[1] + uf2 * tA[2] + kappa * (gT[0] * A[0] + gT[1] * A[1] + gT[2] * A[2]);
+}
+
+// a face between two cells read from global memory (no staging)
+template <typename T>
+__device__ __forceinline__ void face_flux_global(const cell_at<T> &c1, const cell_at<T> &c2, const T fd[kFace], T gam,
+                                                 T mu, T kappa, T out[5])
+{
+    cell_prep<T> p1, p2;
+    prepare_cell(c1, gam, p1);
+    prepare_cell(c2, gam, p2);
+    face_flux(c1, c2, p1, p2, fd, gam, mu, kappa, out);
 }
 
 template <typename T, bool SOA>
@@ -144,7 +184,7 @@ __device__ __forceinline__ T &res_at(T *res, int64_t ncell, int64_t c, int k)
 
 // Shared memory (cap cells, cap_f threads):
 //   ushort4 ge[gw4][cap]   gather only
-//   T cd[28][cap]          FULL only
+//   T cd[32][cap]          FULL only: prepared cells (see cell_prep)
 //   T inc[5][cap]          res prefetched, incremented
 //   T f[5][cap_f]          gather only
 //   int gid[cap]
@@ -161,7 +201,7 @@ __global__ void __launch_bounds__(256) face_flux_hier(const mp_block_desc *__res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ushort4 *s_ge = reinterpret_cast<ushort4 *>(smem_raw);
     T *s_cd = reinterpret_cast<T *>(s_ge + (INC == kIncGather ? gw4 * cap : 0));
-    T *s_inc = s_cd + (FULL ? kCell * cap : 0);
+    T *s_inc = s_cd + (FULL ? kStaged * cap : 0);
     T *s_f = s_inc + 5 * cap;
     int *s_gid = reinterpret_cast<int *>(s_f + (INC == kIncGather ? 5 * cap_f : 0));
 
@@ -191,7 +231,14 @@ __global__ void __launch_bounds__(256) face_flux_hier(const mp_block_desc *__res
         if (FULL) {
             const cell_at<T> src = global_cell<T, SOA>(cdata, ncell, g);
 #pragma unroll 4
-            for (int k = 0; k < kCell; ++k) s_cd[k * cap + i] = src(k);
+            for (int k = 5; k < kCell; ++k) s_cd[k * cap + i] = src(k);
+            cell_prep<T> pc;
+            prepare_cell(src, gam, pc);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) s_cd[v * cap + i] = pc.V[v];
+            s_cd[28 * cap + i] = pc.Tc;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) s_cd[(29 + d) * cap + i] = pc.gT[d];
         }
         if (INC == kIncGather) {
             const ushort4 *row = gat + (int64_t)(d.fp_start[0] + i) * gw4;
@@ -207,10 +254,14 @@ __global__ void __launch_bounds__(256) face_flux_hier(const mp_block_desc *__res
         T fd[kFace];
         load_face<T, SOA>(fdata, nface, f, fd);
         if (FULL) {
-            face_flux(cell_at<T>{s_cd + c1, cap}, cell_at<T>{s_cd + c2, cap}, fd, gam, mu, kappa, F);
+            const cell_at<T> a1{s_cd + c1, cap}, a2{s_cd + c2, cap};
+            cell_prep<T> p1, p2;
+            load_prep(a1, p1);
+            load_prep(a2, p2);
+            face_flux(a1, a2, p1, p2, fd, gam, mu, kappa, F);
         } else {
-            face_flux(global_cell<T, SOA>(cdata, ncell, s_gid[c1]), global_cell<T, SOA>(cdata, ncell, s_gid[c2]), fd,
-                      gam, mu, kappa, F);
+            face_flux_global(global_cell<T, SOA>(cdata, ncell, s_gid[c1]),
+                             global_cell<T, SOA>(cdata, ncell, s_gid[c2]), fd, gam, mu, kappa, F);
         }
     }
     if constexpr (INC == kIncGather) {
@@ -279,7 +330,8 @@ __global__ void __launch_bounds__(256) face_flux_direct(int f0, int f1, const in
     T fd[kFace];
     load_face<T, SOA>(fdata, nface, f, fd);
     T F[5];
-    face_flux(global_cell<T, SOA>(cdata, ncell, cc.x), global_cell<T, SOA>(cdata, ncell, cc.y), fd, gam, mu, kappa, F);
+    face_flux_global(global_cell<T, SOA>(cdata, ncell, cc.x), global_cell<T, SOA>(cdata, ncell, cc.y), fd, gam, mu,
+                     kappa, F);
     if (MODE == kDirectStep1) {
         T *o = out + 10 * f;
 #pragma unroll
@@ -312,12 +364,14 @@ int face_flux_t(const mp_plan *P, const void *fdata, const void *cdata, void *re
     if (co == MP_COLOR_HIER) {
         if (P->opts.block_size > 256) return MP_EINVAL;
         const int cap = P->stats.footprint_max[0];
-        const int variant = mp_staged(P, MP_STAGED_INC_ONLY_GATHER);
+        // default: full staging with thread colours (measured fastest on
+        // GB300, where the 28 values of a cell fit shared memory)
+        const int variant = mp_staged(P, MP_STAGED_SIMPLE);
         const bool full = variant == MP_STAGED_SIMPLE || variant == MP_STAGED_GATHER;
         const bool gather =
             (variant == MP_STAGED_GATHER || variant == MP_STAGED_INC_ONLY_GATHER) && mp_gather_ready(P);
         const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
-        const int smem = cap * (int)((full ? kCell : 0) * sizeof(T) + 5 * sizeof(T) + 4) + gw4 * cap * 8 +
+        const int smem = cap * (int)((full ? kStaged : 0) * sizeof(T) + 5 * sizeof(T) + 4) + gw4 * cap * 8 +
                          cap_f * 5 * (int)sizeof(T);
         auto kern = full ? (gather ? face_flux_hier<T, SOA, true, kIncGather> : face_flux_hier<T, SOA, true, kIncColor>)
                          : (gather ? face_flux_hier<T, SOA, false, kIncGather>

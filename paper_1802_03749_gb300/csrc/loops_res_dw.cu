@@ -21,6 +21,8 @@
 // stores its flux in shared memory, one barrier, and the thread that staged
 // a cell sums that cell's edge fluxes (the plan's block-local inverse map,
 // staged with the cell) and writes it back.
+#include <algorithm>
+
 #include "common.cuh"
 #include "dw.cuh"
 
@@ -31,7 +33,8 @@ namespace {
 //   double res[4]  (prefetched at staging)         (32 B per cell)
 //   dw   rho, ru, rv, E, eps adt/2, u, v, p, H     (9 x 8 B per cell)
 //   dw   inc[4][cap_c]   coloured form             (32 B per cell)
-//        f[4][cap_f]     gather form               (32 B per thread)
+//        f[4][cap_f]     gather form: over the primitives, extended when
+//                        4 cap_f > 9 cap_c
 //   int  gid                                       (4 B per cell)
 //   ushort4 ge[gw4][cap_c]  gather form            (8 gw4 B per cell)
 // The FP64 arrays come first (8-byte alignment).
@@ -70,9 +73,12 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
     float2 *s_v = s_u + cap_c;
     float2 *s_p = s_v + cap_c;
     float2 *s_H = s_p + cap_c;
-    float2 *s_inc = s_H + cap_c;  // [4][cap_c] coloured, [4][cap_f] gather
-    const int inc_stride = GATHER ? cap_f : cap_c;
-    ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_inc + 4 * inc_stride);  // [gw4][cap_c]
+    // increments [4][cap_c] (coloured) after the primitives; the gather
+    // form's fluxes [4][cap_f] overwrite the primitives once all threads
+    // have read them
+    float2 *s_inc = GATHER ? s_r : s_H + cap_c;
+    float2 *s_tail = GATHER ? s_r + max(9 * cap_c, 4 * cap_f) : s_inc + 4 * cap_c;
+    ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_tail);  // [gw4][cap_c]
     int *s_gid = reinterpret_cast<int *>(s_ge + (GATHER ? gw4 * cap_c : 0));
 
     mp_pdl_trigger();
@@ -209,6 +215,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         f[3] = dw_dot_end(A);
     }
     if constexpr (GATHER) {
+        __syncthreads();  // every flux is computed: the primitives are dead
         if (active) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) st(s_inc, k * cap_f + tid, f[k]);
@@ -279,8 +286,9 @@ int res_calc_dw_t(const mp_plan *P, const void *x, const void *q, const void *ad
     const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
     const bool gather = mp_staged(P, MP_STAGED_GATHER) == MP_STAGED_GATHER && mp_gather_ready(P);
     const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
-    const int smem = cap_c * kDwCellBytes + cap_n * kDwNodeBytes + kDwIncBytes * (gather ? cap_f : cap_c) +
-                     8 * gw4 * cap_c;
+    // the gather fluxes reuse the 9 primitive arrays (72 B per cell)
+    const int inc_bytes = gather ? std::max(0, kDwIncBytes * cap_f - 72 * cap_c) : kDwIncBytes * cap_c;
+    const int smem = cap_c * kDwCellBytes + cap_n * kDwNodeBytes + inc_bytes + 8 * gw4 * cap_c;
     auto kern = gather ? res_calc_hier_dw<SOA, true> : res_calc_hier_dw<SOA, false>;
     int rc = mp_allow_smem(kern, smem);
     if (rc != MP_OK) return rc;

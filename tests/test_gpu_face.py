@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-VARIANTS = [("hier", "partition", None), ("hier", "partition", "inc_only"), ("hier", "partition", "simple"),
+VARIANTS = [("hier", "partition", None), ("hier", "partition", "inc_only"), ("hier", "partition", "inc_only_gather"),
             ("hier", "partition", "gather"), ("hier", "rcm", None), ("global", "rcm", None),
             ("atomic", "rcm", None), ("twostep", "rcm", None)]
 
@@ -89,7 +89,7 @@ def test_face_flux_ragged_and_deterministic(ml, block_size):
     ncell, f2c, fd, cd = face_case(11, 6, 5)
     z = np.zeros((ncell, 5))
     ref = oracle.face_flux(f2c, fd, cd)
-    for staged in (None, "inc_only", "simple", "gather"):
+    for staged in (None, "inc_only", "inc_only_gather", "gather"):
         a = run_face(ml, ncell, f2c, fd, cd, z, "hier", "partition", staged, "aos", "f64", block_size=block_size)
         b = run_face(ml, ncell, f2c, fd, cd, z, "hier", "partition", staged, "aos", "f64", block_size=block_size)
         assert rel_l2(a, ref) <= 1e-12 and np.array_equal(a, b), staged
@@ -110,7 +110,8 @@ def test_face_flux_rejects(ml):
 @pytest.mark.slow
 def test_face_flux_full_size(ml):
     """The benchmark's workload: 128^3 hex cells, 6,242,304 faces (the
-    paper's miniAero mesh), FP64, partitioned, block 128, default form;
+    paper's miniAero mesh), FP64, partitioned, block 128, default form
+    (full staging);
     every cell checked."""
     ncell, f2c, fd, cd = face_case(128, 128, 128)
     got = run_face(ml, ncell, f2c, fd, cd, np.zeros((ncell, 5)), "hier", "partition", None, "aos", "f64")
