@@ -124,6 +124,19 @@ __device__ __forceinline__ dw dw_recip(dw x)
     return dw_add(dw{y0, 0.0f}, t);
 }
 
+// The same Newton step with the sloppy additions: 1 - x y0 is computed
+// exactly by them (TwoSum of 1 and the high part is exact by Sterbenz's
+// lemma, then one rounding of the low part), and y0 + t adds a term 2^24
+// times smaller, so neither addition can cancel.
+__device__ __forceinline__ dw dw_recip_fast(dw x)
+{
+    float y0 = __frcp_rn(x.hi);
+    dw p = dw_mul(x, dw{y0, 0.0f});
+    dw e = dw_add_fast(dw{1.0f, 0.0f}, dw_neg(p));
+    dw t = dw_mul(dw{y0, 0.0f}, e);
+    return dw_add_fast(dw{y0, 0.0f}, t);
+}
+
 // Nearest double-word of a double: hi = fl32(d), lo = fl32(d - hi), using
 // the FP64 unit (conversion and subtraction).
 __device__ __forceinline__ dw dw_from_double(double d)

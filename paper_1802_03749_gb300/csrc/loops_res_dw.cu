@@ -129,10 +129,13 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         }
         dw R = dw_from_double_int(r), RU = dw_from_double_int(ru), RV = dw_from_double_int(rv),
            EE = dw_from_double_int(E);
-        dw ri = dw_recip(R);
+        // sloppy additions throughout: the kinetic energy sums two
+        // non-negative terms, E - kin = p/(gam-1) has condition number
+        // 1 + (gam-1) gam M^2 / 2 (1.05 at Mach 0.4), E + p adds positives
+        dw ri = dw_recip_fast(R);
         dw u = dw_mul(RU, ri), v = dw_mul(RV, ri);
-        dw kin = dw_scale2(dw_add(dw_mul(RU, u), dw_mul(RV, v)), 0.5f);
-        dw p = dw_mul(gm1, dw_sub(EE, kin));
+        dw kin = dw_scale2(dw_add_fast(dw_mul(RU, u), dw_mul(RV, v)), 0.5f);
+        dw p = dw_mul(gm1, dw_add_fast(EE, dw_neg(kin)));
         st(s_r, i, R);
         st(s_ru, i, RU);
         st(s_rv, i, RV);
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         st(s_u, i, u);
         st(s_v, i, v);
         st(s_p, i, p);
-        st(s_H, i, dw_add(EE, p));
+        st(s_H, i, dw_add_fast(EE, p));
         if (GATHER) {
             const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
             for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];
