@@ -388,8 +388,8 @@ def bench_hex(ml, torch, timer, args):
         tdt = torch.float64 if dtype == "f64" else torch.float32
         elt = 8 if dtype == "f64" else 4
         for coloring, reorder, variant in (("hier", "partition", "simple"), ("hier", "partition", "smem_atomic"),
-                                           ("atomic", "rcm", None), ("global", "rcm", None),
-                                           ("twostep", "rcm", None)):
+                                           ("hier", "partition", "warp_agg"), ("atomic", "rcm", None),
+                                           ("global", "rcm", None), ("twostep", "rcm", None)):
             H = HexPlan(hm.nnode, hm.elem2node, block_size=256, reorder=reorder, coloring=coloring, staged=variant)
             H.plan.upload()
             x = torch.tensor(H.to_plan(hm.x, "node"), dtype=tdt, device="cuda")
@@ -645,6 +645,9 @@ def main():
                 ("two_layer_rcm", "hier", "rcm", compute, args.staged), ("global_rcm", "global", "rcm", None, None),
                 ("global_none", "global", "none", None, None), ("atomic_rcm", "atomic", "rcm", None, None),
                 ("atomic_none", "atomic", "none", None, None), ("twostep_rcm", "twostep", "rcm", None, None)]
+        pre = "two_layer_partition_" + ("native_f64_" if compute else "")
+        todo += [(pre + "smem_atomic", "hier", "partition", None, "smem_atomic"),
+                 (pre + "warp_agg", "hier", "partition", None, "warp_agg")]
         if compute == "dw":
             todo.insert(1, ("two_layer_partition_native_f64", "hier", "partition", None, None))
             todo.insert(2, ("two_layer_partition_native_f64_gather", "hier", "partition", None, "gather"))

@@ -112,8 +112,9 @@ typedef struct {
     int32_t data_reorder;/* 1: reorder to-set points by accessing blocks (Sec. 2.3.2);
                             -1: default (on with MP_REORDER_PARTITION)              */
     int32_t staged;      /* MP_STAGED_* implementation of HIER loops; -1: the loop's
-                            default (MP_STAGED_SMEM_ATOMIC for hex assembly, whose 3D
-                            blocks need ~10 thread colours; MP_STAGED_GATHER for FP32
+                            default (hex assembly, whose 3D blocks need ~10 thread
+                            colours: MP_STAGED_SMEM_ATOMIC in FP32, MP_STAGED_WARP_AGG
+                            in FP64; MP_STAGED_GATHER for FP32
                             and double-word res_calc and the increment-only loops;
                             MP_STAGED_SIMPLE otherwise)                               */
     int32_t recolor;     /* HIER: after the first-fit block colouring, empty the last
@@ -274,7 +275,12 @@ int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void 
  *    double-word res_calc or the adjoint, which run SIMPLE.
  * Block colouring orders the write-back in every variant.                */
 enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2, MP_STAGED_GATHER = 3,
-       MP_STAGED_INC_ONLY = 4, MP_STAGED_INC_ONLY_GATHER = 5 };
+       MP_STAGED_INC_ONLY = 4, MP_STAGED_INC_ONLY_GATHER = 5, MP_STAGED_WARP_AGG = 6 };
+/* MP_STAGED_WARP_AGG: warp-aggregated increments: lanes of a warp that
+ * increment the same point combine their values with a segmented shuffle
+ * tree (match.any groups) and one lane adds the sum with a shared-memory
+ * atomic; one barrier, order across warps not fixed.  res_calc (native
+ * FP64 and FP32) and hex assembly.                                        */
 /* MP_STAGED_INC_ONLY(_GATHER): shared memory caches only the increments (and
  * the current values they add to); the loop reads its indirect inputs
  * through L1/L2 instead of staging them (Sec. 3.1.5: for loops whose

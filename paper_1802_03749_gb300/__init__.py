@@ -36,7 +36,7 @@ MP_MAX_MAPS = 4
 MP_MAX_TOSETS = 2
 REORDER = {"none": 0, "rcm": 1, "partition": 2}
 STAGED = {None: -1, "pipelined": 0, "simple": 1, "smem_atomic": 2, "gather": 3, "inc_only": 4,
-          "inc_only_gather": 5}
+          "inc_only_gather": 5, "warp_agg": 6}
 COLORING = {"hier": 0, "global": 1, "atomic": 2, "twostep": 3}
 LAYOUT = {"aos": 0, "soa": 1}
 DTYPE = {"f64": 0, "f32": 1, "f64dw": 2}

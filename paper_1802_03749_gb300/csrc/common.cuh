@@ -39,6 +39,34 @@ inline bool mp_pdl_enabled()
 __device__ __forceinline__ void mp_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void mp_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Warp-aggregated increment: the lanes of a warp that target the same
+// point (found with match.any) sum their values by a segmented shuffle
+// tree in rank order and the lowest of them adds the sum with one
+// shared-memory atomic.  All lanes of `act` must call it (uniform trip
+// count: the largest group decides the tree depth).
+template <typename T, int N>
+__device__ __forceinline__ void warp_aggregated_add(unsigned act, int target, T v[N], T *base, int stride)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(act, target);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const unsigned widest = __reduce_max_sync(act, (unsigned)__popc(peers));
+    for (unsigned off = 1; off < widest; off <<= 1) {
+        const unsigned src = __fns(peers, lane, off + 1);  // the peer off ranks above
+        const bool take = (rank % (2 * off)) == 0 && src != 0xffffffffu;
+        const int from = src != 0xffffffffu ? (int)src : lane;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const T y = __shfl_sync(act, v[k], from);
+            if (take) v[k] += y;
+        }
+    }
+    if (rank == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) atomicAdd(base + k * stride + target, v[k]);
+    }
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t mp_launch(void (*kern)(KArgs...), int grid, int block, int smem, cudaStream_t s, bool overlap,
                       Args... args)

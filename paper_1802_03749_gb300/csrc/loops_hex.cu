@@ -117,7 +117,9 @@ __host__ __device__ constexpr int hex_smem_per_node()
     return 9 * (int)sizeof(T) + 4;
 }
 
-template <typename T, bool SOA, bool SMEM_ATOMIC>
+// increments: 0 thread colours, 1 shared-memory atomics, 3 warp-aggregated
+// shared-memory atomics
+template <typename T, bool SOA, int INC>
 __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict__ desc, int block0,
                                                 const uint4 *__restrict__ lmap, const uint8_t *__restrict__ tcolor,
                                                 const int32_t *__restrict__ fp, const T *__restrict__ x,
@@ -194,7 +196,14 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
         vol[e] = V;
     }
-    if (SMEM_ATOMIC) {  // shared-memory atomics instead of thread colours
+    if (INC == 3) {  // warp-aggregated shared-memory atomics
+        const unsigned act = __ballot_sync(0xffffffffu, active);
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) warp_aggregated_add<T, 3>(act, loc[i], fe[i], s_f, cap);
+        }
+        __syncthreads();
+    } else if (INC == 1) {  // shared-memory atomics instead of thread colours
         if (active) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -304,8 +313,12 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
     if (P->opts.coloring == MP_COLOR_HIER) {
         const int cap = P->stats.footprint_max[0];
         const int smem = cap * hex_smem_per_node<T>();
-        auto kern = mp_staged(P, MP_STAGED_SMEM_ATOMIC) == MP_STAGED_SMEM_ATOMIC ? hex_hier<T, SOA, true>
-                                                                                 : hex_hier<T, SOA, false>;
+        // default increments: shared-memory atomics in FP32, warp-aggregated
+        // ones in FP64 (whose shared-memory atomics are slower; measured)
+        const int variant = mp_staged(P, sizeof(T) == 8 ? MP_STAGED_WARP_AGG : MP_STAGED_SMEM_ATOMIC);
+        auto kern = variant == MP_STAGED_SMEM_ATOMIC ? hex_hier<T, SOA, 1>
+                    : variant == MP_STAGED_WARP_AGG  ? hex_hier<T, SOA, 3>
+                                                     : hex_hier<T, SOA, 0>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
         int *err = nullptr;

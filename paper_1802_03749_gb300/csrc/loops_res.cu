@@ -34,6 +34,8 @@ namespace {
 //               sums the fluxes of its edges in the block from the plan's
 //               block-local inverse map (fixed order: deterministic) and is
 //               written back by the same thread
+//   kIncShuffle warp-aggregated atomics: lanes of a warp with the same
+//               target reduce by shuffles, one atomic per target and warp
 template <typename T>
 __host__ __device__ constexpr int res_smem_per_cell()
 {
@@ -44,7 +46,8 @@ __host__ __device__ constexpr int res_smem_per_node()
 {
     return 2 * (int)sizeof(T);
 }
-constexpr int kIncColor = 0, kIncAtomic = 1, kIncGather = 2;
+constexpr int kIncColor = 0, kIncAtomic = 1, kIncGather = 2, kIncShuffle = 3;
+
 
 template <typename T, bool SOA>
 __device__ __forceinline__ void load_res(const T *__restrict__ res, int64_t ncell, int g, T &r0, T &r1, T &r2, T &r3)
@@ -243,7 +246,16 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         }
         return;
     }
-    if (INC == kIncAtomic) {
+    if (INC == kIncShuffle) {
+        // warp-aggregated shared-memory atomics: one barrier
+        const unsigned act = __ballot_sync(0xffffffffu, active);
+        if (active) {
+            T g[4] = {-f[0], -f[1], -f[2], -f[3]};
+            warp_aggregated_add<T, 4>(act, c1, f, s_inc, cap_c);
+            warp_aggregated_add<T, 4>(act, c2, g, s_inc, cap_c);
+        }
+        __syncthreads();
+    } else if (INC == kIncAtomic) {
         // shared-memory atomics instead of thread colours: one barrier
         if (active) {
 #pragma unroll
@@ -507,6 +519,7 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
                          4 * cap_f * (int)sizeof(T);
         auto kern = gather                                 ? res_calc_hier<T, SOA, kIncGather>
                     : variant == MP_STAGED_SMEM_ATOMIC ? res_calc_hier<T, SOA, kIncAtomic>
+                    : variant == MP_STAGED_WARP_AGG    ? res_calc_hier<T, SOA, kIncShuffle>
                                                        : res_calc_hier<T, SOA, kIncColor>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;

@@ -66,12 +66,14 @@ def test_hex_block_sizes_ragged(block_size):
     assert rel_l2(f, fr) <= 1e-12 and rel_l2(vol, vr) <= 1e-12
 
 
+@pytest.mark.parametrize("staged", ["simple", "warp_agg"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_hex_thread_coloured_variant(dtype):
+def test_hex_thread_coloured_variant(dtype, staged):
     """Hex assembly defaults to shared-memory atomics; the thread-coloured
-    increments of Algorithm 1 are the other staged variant."""
+    increments of Algorithm 1 and the warp-aggregated atomics are the other
+    staged variants."""
     m, sig, v = case(14)
-    f, vol, _ = run_hex(m, sig, v, "hier", "partition", "aos", dtype, staged="simple")
+    f, vol, _ = run_hex(m, sig, v, "hier", "partition", "aos", dtype, staged=staged)
     if dtype == "f64":
         fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
         assert rel_l2(f, fr) <= 1e-12
