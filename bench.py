@@ -297,16 +297,19 @@ def bench_face(ml, torch, timer, args):
     rows = {}
 
     def measure(S, name, dtype):
-        tdt = torch.float64 if dtype == "f64" else torch.float32
-        elt = 8 if dtype == "f64" else 4
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        elt = 4 if dtype == "f32" else 8
+        comp = "dw" if dtype == "f64dw" else None
         fdd = torch.tensor(S.to_plan(fd, "from"), dtype=tdt, device="cuda")
         cdd = torch.tensor(S.to_plan(cd, "to"), dtype=tdt, device="cuda")
         res = torch.zeros((nc, 5), dtype=tdt, device="cuda")
-        ms, _ = timer(lambda: ml.loop_face_flux(S.plan, fdd, cdd, res), 10, 2)
+        ms, _ = timer(lambda: ml.loop_face_flux(S.plan, fdd, cdd, res, compute=comp), 10, 2)
         ub = nf * (12 * elt + 8) + nc * (28 * elt + 2 * 5 * elt)
         st = S.plan.stats()
         rows[f"face_{dtype}_{name}"] = {
-            "workload": f"miniAero-style face flux, {nc} hex cells, {nf} faces, {dtype.upper()}", "ms": ms,
+            "workload": f"miniAero-style face flux, {nc} hex cells, {nf} faces, "
+                        + {"f64": "FP64", "f32": "FP32", "f64dw": "FP64 data, double-word arithmetic"}[dtype],
+            "ms": ms,
             "gfaces_s": nf / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
             "block_colors": st["nblock_colors"], "reuse": st["reuse_all"]}
         del fdd, cdd, res
@@ -317,6 +320,7 @@ def bench_face(ml, torch, timer, args):
         S.plan.set_staged(staged)
         measure(S, f"hier_partition_{staged}", "f64")
     S.plan.set_staged(None)
+    measure(S, "hier_partition_simple", "f64dw")
     measure(S, "hier_partition_simple", "f32")
     del S
     for coloring in ("hier", "global", "atomic", "twostep"):

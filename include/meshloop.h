@@ -407,7 +407,9 @@ int loop_getacc(const mp_plan *plan, int32_t dtype, const void *cdata, void *nd,
  * MP_STAGED_SIMPLE: the 28 cell values staged and prepared once per cell,
  * thread-coloured increments; MP_STAGED_GATHER likewise with gather
  * increments; MP_STAGED_INC_ONLY[_GATHER] stage the increments only),
- * GLOBAL, ATOMIC or TWOSTEP (the original code's temporary array).  dtype MP_F64 or MP_F32.  fdata [faces][12], cdata
+ * GLOBAL, ATOMIC or TWOSTEP (the original code's temporary array).  dtype MP_F64, MP_F32 or MP_F64_DW (HIER
+ * plans, block size <= 128: FP64 data, double-word arithmetic, full staging
+ * and thread-coloured increments).  fdata [faces][12], cdata
  * [cells][28], res [cells][5] (SoA: transposed); device memory in plan
  * numbering, 16-byte aligned.  Errors: MP_EINVAL (dtype, constants, null or
  * misaligned pointer, block size), MP_EPLAN (plan shape), MP_ECUDA.       */

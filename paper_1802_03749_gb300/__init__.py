@@ -398,9 +398,14 @@ def loop_getacc(plan: Plan, cdata, nd, stream=None):
 
 
 def loop_face_flux(plan: Plan, fdata, cdata, res, gam: float = 1.4, mu: float = 1e-3, pr: float = 0.72,
-                   stream=None):
-    """Face flux (miniAero-style, Sec. 3.1.5); res [cells][5] +=."""
+                   stream=None, compute: str | None = None):
+    """Face flux (miniAero-style, Sec. 3.1.5); res [cells][5] +=.  ``compute="dw"``
+    selects double-word arithmetic on FP64 data (HIER plans, block <= 128)."""
     dt = _dtype_of(fdata, cdata, res)
+    if compute == "dw":
+        if dt != DTYPE["f64"]:
+            raise MeshLoopError(-1, "double-word arithmetic needs float64 data")
+        dt = DTYPE["f64dw"]
     _check(lib().loop_face_flux(plan.handle, dt, _ptr(fdata), _ptr(cdata), _ptr(res), gam, mu, pr,
                                 _stream(stream)), "loop_face_flux")
 

@@ -127,6 +127,8 @@ int mp_res_calc_dw(const mp_plan *P, const void *x, const void *q, const void *a
                    void *stream);
 
 // Two-layer hex assembly with FP64 data and double-word arithmetic.
+int mp_face_flux_dw(const mp_plan *P, const void *fdata, const void *cdata, void *res, double gam, double mu,
+                    double pr, void *stream);
 int mp_hex_dw(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, double kappa,
               void *stream);
 

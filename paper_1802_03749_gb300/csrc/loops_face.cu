@@ -419,13 +419,21 @@ int face_flux_t(const mp_plan *P, const void *fdata, const void *cdata, void *re
 extern "C" int loop_face_flux(const mp_plan *P, int32_t dtype, const void *fdata, const void *cdata, void *res,
                               double gam, double mu, double pr, void *stream)
 {
-    if (!P || (dtype != MP_F64 && dtype != MP_F32) || !(gam > 1.0) || !(mu >= 0.0) || !(pr > 0.0)) return MP_EINVAL;
+    if (!P || (dtype != MP_F64 && dtype != MP_F32 && dtype != MP_F64_DW) || !(gam > 1.0) || !(mu >= 0.0) ||
+        !(pr > 0.0))
+        return MP_EINVAL;
     if (P->nmaps != 1 || P->maps[0].arity != 2 || !P->maps[0].written) return MP_EPLAN;
     if (P->from_size == 0) return MP_OK;
     for (const void *p : {fdata, cdata, (const void *)res})
         if (!p || !aligned16(p)) return MP_EINVAL;
     int rc = mp_plan_ensure_device(P);
     if (rc != MP_OK) return rc;
+    if (dtype == MP_F64_DW) {
+        rc = mp_face_flux_dw(P, fdata, cdata, res, gam, mu, pr, stream);
+        if (rc != MP_OK) return rc;
+        MP_CUDA_TRY(cudaGetLastError());
+        return MP_OK;
+    }
     cudaStream_t s = as_stream(stream);
     const bool soa = P->opts.layout == MP_LAYOUT_SOA;
     if (dtype == MP_F64)

@@ -54,14 +54,14 @@ def flux_scale(f2c, fd, cd):
     return S
 
 
-def run_face(ml, ncell, f2c, fd, cd, r0, coloring, reorder, staged, layout, dtype, block_size=128):
+def run_face(ml, ncell, f2c, fd, cd, r0, coloring, reorder, staged, layout, dtype, block_size=128, compute=None):
     from paper_1802_03749_gb300.mesh import ScatterPlan
     S = ScatterPlan(ncell, f2c, block_size=block_size, reorder=reorder, coloring=coloring, layout=layout,
                     staged=staged)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     t = lambda a, w: torch.tensor(S.to_plan(a, w), dtype=tdt, device="cuda")
     res = t(r0, "to")
-    ml.loop_face_flux(S.plan, t(fd, "from"), t(cd, "to"), res)
+    ml.loop_face_flux(S.plan, t(fd, "from"), t(cd, "to"), res, compute=compute)
     torch.cuda.synchronize()
     ml.mp_check_device_status()
     return S.from_plan(res.cpu().numpy().astype(np.float64), "to", 5)
@@ -107,13 +107,39 @@ def test_face_flux_rejects(ml):
         ml.loop_face_flux(T.plan, z, z, z, gam=1.0)
 
 
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("reorder", ["partition", "rcm", "none"])
+def test_face_flux_double_word_parity(ml, reorder, layout):
+    """FP64 data, double-word arithmetic: within the FP64 bar."""
+    ncell, f2c, fd, cd = face_case(13, 9, 7)
+    r0 = 0.01 * np.cos(np.arange(5 * ncell)).reshape(-1, 5)
+    got = run_face(ml, ncell, f2c, fd, cd, r0, "hier", reorder, None, layout, "f64", compute="dw")
+    ref = oracle.face_flux(f2c, fd, cd, res=r0)
+    assert rel_l2(got - r0, ref - r0) <= 1e-12
+
+
+@pytest.mark.parametrize("block_size", [32, 64, 128])
+def test_face_flux_double_word_ragged_and_deterministic(ml, block_size):
+    ncell, f2c, fd, cd = face_case(11, 6, 5)
+    z = np.zeros((ncell, 5))
+    ref = oracle.face_flux(f2c, fd, cd)
+    a = run_face(ml, ncell, f2c, fd, cd, z, "hier", "partition", None, "aos", "f64", block_size=block_size,
+                 compute="dw")
+    b = run_face(ml, ncell, f2c, fd, cd, z, "hier", "partition", None, "aos", "f64", block_size=block_size,
+                 compute="dw")
+    assert rel_l2(a, ref) <= 1e-12 and np.array_equal(a, b)
+
+
 @pytest.mark.slow
 def test_face_flux_full_size(ml):
     """The benchmark's workload: 128^3 hex cells, 6,242,304 faces (the
-    paper's miniAero mesh), FP64, partitioned, block 128, default form
-    (full staging);
+    paper's miniAero mesh), FP64 data in FP64 and in double-word
+    arithmetic, partitioned, block 128, default form (full staging);
     every cell checked."""
     ncell, f2c, fd, cd = face_case(128, 128, 128)
-    got = run_face(ml, ncell, f2c, fd, cd, np.zeros((ncell, 5)), "hier", "partition", None, "aos", "f64")
-    assert rel_l2(got, oracle.face_flux(f2c, fd, cd)) <= 1e-12
+    ref = oracle.face_flux(f2c, fd, cd)
+    for compute in (None, "dw"):
+        got = run_face(ml, ncell, f2c, fd, cd, np.zeros((ncell, 5)), "hier", "partition", None, "aos", "f64",
+                       compute=compute)
+        assert rel_l2(got, ref) <= 1e-12, compute
     CASES.clear()
