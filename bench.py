@@ -410,22 +410,27 @@ def bench_hex(ml, torch, timer, args):
                 "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
                 "reuse": st["reuse_all"]}
             del x, vd, sd, f, vol
-    # hex assembly with FP64 data in double-word arithmetic (two-layer, S = 128)
-    H = HexPlan(hm.nnode, hm.elem2node, block_size=128, reorder="rcm", coloring="hier")
-    H.plan.upload()
-    x = torch.tensor(H.to_plan(hm.x, "node"), device="cuda")
-    vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
-    sd = torch.tensor(H.to_plan(sig, "elem"), device="cuda")
-    f = torch.zeros_like(x)
-    vol = torch.zeros(hm.nelem, dtype=torch.float64, device="cuda")
-    ms, _ = timer(lambda: ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01, compute="dw"), 10, 2)
-    ub = useful_bytes_hex(hm.nelem, hm.nnode, 8)
-    st = H.plan.stats()
-    rows["hex_f64dw_hier_rcm"] = {
-        "workload": f"hex assembly {args.hex_n}^3 elements, double-word arithmetic", "ms": ms,
-        "gelems_s": hm.nelem / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
-        "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"], "reuse": st["reuse_all"]}
-    del x, vd, sd, f, vol
+    # hex assembly with FP64 data in double-word arithmetic (two-layer, S = 128):
+    # gather increments (default) and thread colours, partitioned and RCM
+    for reorder in ("partition", "rcm"):
+        H = HexPlan(hm.nnode, hm.elem2node, block_size=128, reorder=reorder, coloring="hier")
+        H.plan.upload()
+        x = torch.tensor(H.to_plan(hm.x, "node"), device="cuda")
+        vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
+        sd = torch.tensor(H.to_plan(sig, "elem"), device="cuda")
+        f = torch.zeros_like(x)
+        vol = torch.zeros(hm.nelem, dtype=torch.float64, device="cuda")
+        ub = useful_bytes_hex(hm.nelem, hm.nnode, 8)
+        st = H.plan.stats()
+        for staged in ("gather", "simple"):
+            H.plan.set_staged(staged)
+            ms, _ = timer(lambda: ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01, compute="dw"), 10, 2)
+            rows[f"hex_f64dw_hier_{reorder}_{staged}"] = {
+                "workload": f"hex assembly {args.hex_n}^3 elements, double-word arithmetic", "ms": ms,
+                "gelems_s": hm.nelem / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
+                "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
+                "reuse": st["reuse_all"]}
+        del x, vd, sd, f, vol
     return rows
 
 
@@ -472,16 +477,18 @@ def bench_adjoint(ml, torch, timer, args):
     aq = meshgen.quad_state(am.ncell)
     aadt = synthetic_adt(am)
     rb = meshgen.adjoint_seed(am.ncell)
-    for coloring, reorder, comp in (("hier", "partition", None), ("hier", "partition", "dw"), ("atomic", "rcm", None)):
+    for coloring, reorder, comp, staged in (("hier", "partition", None, None), ("hier", "partition", "dw", "gather"),
+                                            ("hier", "partition", "dw", "simple"), ("atomic", "rcm", None, None)):
         P = AirfoilPlans(am.ncell, am.nnode, am.edge2node, am.edge2cell, am.bedge2node, am.bedge2cell, am.cell2node,
-                         block_size=256 if comp else 384, reorder=reorder, coloring=coloring, adjoint=True)
+                         block_size=256 if comp else 384, reorder=reorder, coloring=coloring, adjoint=True,
+                         staged=staged)
         P.res.upload()
         t = lambda a, w: torch.tensor(P.to_plan(a, w), device="cuda")
         x, qd, ad, rbd = t(am.x, "node"), t(aq, "cell"), t(aadt, "cell"), t(rb, "cell")
         qb, xb = torch.zeros_like(qd), torch.zeros_like(x)
         ms, _ = timer(lambda: ml.loop_adjoint(P.res, x, qd, ad, rbd, qb, xb, compute=comp), 10, 2)
         ub = useful_bytes_adjoint(am.ncell, am.nnode, am.nedge)
-        rows[f"adjoint_{'f64dw' if comp else 'f64'}_{coloring}_{reorder}"] = {
+        rows[f"adjoint_{'f64dw' if comp else 'f64'}_{coloring}_{reorder}" + (f"_{staged}" if staged else "")] = {
             "workload": "res_calc adjoint 1200x600", "ms": ms, "gedges_s": am.nedge / ms / 1e6,
             "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm}
     return rows

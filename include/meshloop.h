@@ -84,9 +84,10 @@ enum { MP_LAYOUT_AOS = 0, MP_LAYOUT_SOA = 1 };
 enum { MP_F64 = 0, MP_F32 = 1, MP_F64_DW = 2 };
 /* MP_F64_DW: FP64 data, arithmetic in double-word (pairs of FP32, ~48-bit
  * significand) on the FP32 pipes; results agree with FP64 to ~1e-13
- * relative.  Offered by loop_res_calc, loop_adjoint and loop_elem_assemble
- * with HIER plans (thread-coloured increments; hex: blocks of at most 256
- * threads).                                                              */
+ * relative.  Offered by loop_res_calc, loop_adjoint, loop_elem_assemble and
+ * loop_face_flux with HIER plans (res_calc and hex assembly: gather
+ * increments by default, MP_STAGED_SIMPLE for thread colours; hex: blocks
+ * of at most 256 threads; face flux: at most 128).                       */
 
 /* One map of the loop: from the loop's iteration set (set id 0) to the
  * caller's set `to_set` (ids >= 1; maps with the same id share a to-set).

@@ -10,6 +10,8 @@
 //   n_b += (h1 p + Wb rho u,  h2 p + Wb rho v),
 // plus mu f_bar on q1 and -mu f_bar on q2; each component is one
 // compensated sum of products.  The edge normal is formed in FP64.
+#include <algorithm>
+
 #include "common.cuh"
 #include "dw.cuh"
 
@@ -29,6 +31,8 @@ __device__ __forceinline__ void stw(float2 *a, int i, dw v) { a[i] = make_float2
 //                                          a' = eps adt / 2)
 //   dw rb[4], qinc[4]                     (64 B per cell)
 //   dw xinc[2]                            (16 B per node)
+//   (gather form: no qinc / xinc; a [10][cap_f] buffer of per-edge
+//    increments over the cell arrays and rb, then the gather rows)
 //   int gid per cell and node
 constexpr int kAdjDwCellBytes = 32 + 80 + 64 + 4;
 constexpr int kAdjDwNodeBytes = 32 + 16 + 4;
@@ -75,10 +79,14 @@ __device__ __forceinline__ void flux_rev_dw(const float2 *const S[10], int c, dw
     dw_dot_add(nby, Wb, rv);
 }
 
-template <bool SOA>
+// GATHER: the per-edge adjoint increments (q_bar of both cells, the normal
+// adjoint) go to a shared buffer over the dead staged cell data, and each
+// cell and node sums its edges' entries through the plan's gather rows.
+template <bool SOA, bool GATHER>
 __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
                                                           const ushort4 *__restrict__ lmap,
                                                           const uint8_t *__restrict__ tcolor,
+                                                          const ushort4 *__restrict__ gat, int gw4, int cap_f,
                                                           const int32_t *__restrict__ fp, const double *__restrict__ x,
                                                           const double *__restrict__ q,
                                                           const double *__restrict__ adt,
@@ -93,9 +101,12 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
     double *s_qb = s_xb + 2 * cap_n;                      // [4][cap_c] q_bar (FP64, prefetched)
     float2 *s_cell = reinterpret_cast<float2 *>(s_qb + 4 * cap_c);  // [10][cap_c]
     float2 *s_rb = s_cell + 10 * cap_c;                   // [4][cap_c]
-    float2 *s_qi = s_rb + 4 * cap_c;                      // [4][cap_c] q_bar increments
-    float2 *s_xi = s_qi + 4 * cap_c;                      // [2][cap_n] x_bar increments
-    int *s_gc = reinterpret_cast<int *>(s_xi + 2 * cap_n);
+    float2 *s_qi = s_rb + 4 * cap_c;                      // coloured: [4][cap_c] q_bar increments
+    float2 *s_xi = s_qi + 4 * cap_c;                      // coloured: [2][cap_n] x_bar increments
+    // gather: [10][cap_f] per-edge increments over s_cell and s_rb, rows
+    float2 *s_fb = s_cell;
+    ushort4 *s_ge = reinterpret_cast<ushort4 *>(GATHER ? s_cell + max(14 * cap_c, 10 * cap_f) : s_xi + 2 * cap_n);
+    int *s_gc = reinterpret_cast<int *>(s_ge + (GATHER ? gw4 * (cap_c + cap_n) : 0));
     int *s_gn = s_gc + cap_c;
     const float2 *S[10];
 #pragma unroll
@@ -106,7 +117,8 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0], nc = d.fp_count[1];
     if ((unsigned)(reinterpret_cast<unsigned char *>(s_gn + cap_n) - smem_raw) > dynamic_smem_bytes() ||
-        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x) {
+        nc > cap_c || nn > cap_n || d.nitems > (int)blockDim.x ||
+        (GATHER && ((int)blockDim.x > cap_f || gw4 < 1 || gw4 > 4))) {
         if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
         return;
     }
@@ -117,7 +129,7 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
     int my_color = -1;
     if (active) {
         l = lmap[d.item_start + tid];
-        my_color = tcolor[d.item_start + tid];
+        if (!GATHER) my_color = tcolor[d.item_start + tid];
     }
     for (int i = tid; i < nc; i += blockDim.x) {
         const int64_t g = fpc[i];
@@ -127,7 +139,7 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
             const int64_t j = SOA ? k * ncell + g : 4 * g + k;
             qq[k] = dw_from_double_int(q[j]);
             stw(s_rb, k * cap_c + i, dw_from_double_int(rbar[j]));
-            s_qi[k * cap_c + i] = make_float2(0.f, 0.f);
+            if (!GATHER) s_qi[k * cap_c + i] = make_float2(0.f, 0.f);
         }
         mp_pdl_wait();  // q_bar, x_bar: written by the previous colour's launch
 #pragma unroll
@@ -149,6 +161,10 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         stw(W, 7 * cap_c + i, p);
         stw(W, 8 * cap_c + i, K);
         stw(W, 9 * cap_c + i, dw_mul(dw_from_double_int(adt[g]), half_eps));
+        if (GATHER) {
+            const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
+            for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];  // cell rows
+        }
         s_gc[i] = (int)g;
     }
     for (int i = tid; i < nn; i += blockDim.x) {
@@ -158,8 +174,13 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         mp_pdl_wait();
         s_xb[i] = SOA ? xbar[g] : xbar[2 * g];
         s_xb[cap_n + i] = SOA ? xbar[nnode + g] : xbar[2 * g + 1];
-        s_xi[i] = make_float2(0.f, 0.f);
-        s_xi[cap_n + i] = make_float2(0.f, 0.f);
+        if (GATHER) {
+            const ushort4 *row = gat + (int64_t)(d.fp_start[0] + i) * gw4;
+            for (int h = 0; h < gw4; ++h) s_ge[gw4 * cap_c + h * cap_n + i] = row[h];  // node rows
+        } else {
+            s_xi[i] = make_float2(0.f, 0.f);
+            s_xi[cap_n + i] = make_float2(0.f, 0.f);
+        }
         s_gn[i] = (int)g;
     }
     __syncthreads();
@@ -191,6 +212,63 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
             qb2[k] = dw_add_fast(qb2[k], dw_neg(m));
         }
     }
+    if constexpr (GATHER) {
+        __syncthreads();  // every edge is computed: the staged cell data are dead
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                stw(s_fb, k * cap_f + tid, qb1[k]);
+                stw(s_fb, (4 + k) * cap_f + tid, qb2[k]);
+            }
+            stw(s_fb, 8 * cap_f + tid, nbx);
+            stw(s_fb, 9 * cap_f + tid, nby);
+        }
+        __syncthreads();
+        // cells: q_bar of the edges' first (map slot 2) or second (slot 3) cell
+        for (int i = tid; i < nc; i += blockDim.x) {
+            dw a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            for (int h = 0; h < gw4; ++h) {
+                const ushort4 e4 = s_ge[h * cap_c + i];
+                const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned en = es[j];
+                    if (en == 0xFFFFu) continue;
+                    const int t = (int)(en >> 4), base = (en & 15u) == 3u ? 4 : 0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) a[k] = dw_add_fast(a[k], ldw(s_fb, (base + k) * cap_f + t));
+                }
+            }
+            const int64_t g = s_gc[i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qbar[SOA ? k * ncell + g : 4 * g + k] = f64_add_dw(s_qb[k * cap_c + i], a[k]);
+        }
+        // nodes: node a (slot 0) gets (-n_y_bar, n_x_bar), node b (slot 1) the opposite
+        for (int i = tid; i < nn; i += blockDim.x) {
+            dw ax = {0.f, 0.f}, ay = {0.f, 0.f};
+            for (int h = 0; h < gw4; ++h) {
+                const ushort4 e4 = s_ge[gw4 * cap_c + h * cap_n + i];
+                const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned en = es[j];
+                    if (en == 0xFFFFu) continue;
+                    const int t = (int)(en >> 4);
+                    const dw bx = ldw(s_fb, 8 * cap_f + t), by = ldw(s_fb, 9 * cap_f + t);
+                    if ((en & 15u) == 0u) {
+                        ax = dw_add_fast(ax, dw_neg(by));
+                        ay = dw_add_fast(ay, bx);
+                    } else {
+                        ax = dw_add_fast(ax, by);
+                        ay = dw_add_fast(ay, dw_neg(bx));
+                    }
+                }
+            }
+            const int64_t g = s_gn[i];
+            xbar[SOA ? g : 2 * g] = f64_add_dw(s_xb[i], ax);
+            xbar[SOA ? nnode + g : 2 * g + 1] = f64_add_dw(s_xb[cap_n + i], ay);
+        }
+    } else {
     for (int c = 0; c < d.ncolors; ++c) {
         if (my_color == c) {
 #pragma unroll
@@ -217,6 +295,7 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         xbar[SOA ? g : 2 * g] = f64_add_dw(s_xb[i], ldw(s_xi, i));
         xbar[SOA ? nnode + g : 2 * g + 1] = f64_add_dw(s_xb[cap_n + i], ldw(s_xi, cap_n + i));
     }
+    }
 }
 
 template <bool SOA>
@@ -227,8 +306,14 @@ int adjoint_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt
     if (P->opts.block_size > 512) return MP_EINVAL;
     const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
     const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
-    const int smem = cap_c * kAdjDwCellBytes + cap_n * kAdjDwNodeBytes;
-    auto kern = adjoint_hier_dw<SOA>;
+    const bool gather = mp_staged(P, MP_STAGED_GATHER) == MP_STAGED_GATHER && mp_gather_ready(P);
+    const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
+    // gather: no increment arrays (32 B per cell, 16 B per node); the edge
+    // buffer (80 B per thread) reuses the staged cell data (112 B per cell)
+    const int smem = gather ? cap_c * (kAdjDwCellBytes - 32) + cap_n * (kAdjDwNodeBytes - 16) +
+                                  std::max(0, 80 * cap_f - 112 * cap_c) + 8 * gw4 * (cap_c + cap_n)
+                            : cap_c * kAdjDwCellBytes + cap_n * kAdjDwNodeBytes;
+    auto kern = gather ? adjoint_hier_dw<SOA, true> : adjoint_hier_dw<SOA, false>;
     int rc = mp_allow_smem(kern, smem);
     if (rc != MP_OK) return rc;
     int *err = nullptr;
@@ -241,7 +326,8 @@ int adjoint_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt
         const int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
         if (nb == 0) continue;
         MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
-                              reinterpret_cast<const ushort4 *>(P->dev.lmap), P->dev.tcolor, P->dev.fp,
+                              reinterpret_cast<const ushort4 *>(P->dev.lmap), P->dev.tcolor,
+                              reinterpret_cast<const ushort4 *>(P->dev.gat), gw4, cap_f, P->dev.fp,
                               (const double *)x, (const double *)q, (const double *)adt, (const double *)rbar,
                               (double *)qbar, (double *)xbar, nnode, ncell, cap_c, cap_n, gm1, half_eps, err));
         overlap = true;

@@ -5,8 +5,10 @@
 // Staged two-layer structure as hex_hier: the block's node footprint (x, v
 // converted to double-word, and the current f in FP64) is staged in shared
 // memory; each thread computes one element's forces in double-word
-// arithmetic; the 24 increments accumulate in double-word in shared memory
-// one thread colour at a time; each footprint node's f is written back once
+// arithmetic; the 24 increments either go to a shared force buffer that
+// each node then sums through the plan's gather rows (the default), or
+// accumulate in shared memory one thread colour at a time (MP_STAGED_SIMPLE);
+// each footprint node's f is written back once
 // (FP64 + double-word, two FP64 additions).  Element volumes are written
 // directly.  The formulas are those of the FP64 kernel (loops_hex.cu).
 #include "common.cuh"
@@ -34,31 +36,60 @@ __device__ __forceinline__ dw dw_det2(dw a, dw b, dw c, dw d)
     return dw_dot_end(A);
 }
 
-// smem per footprint node: x[3], v[3], increments[3] as double-word (72 B),
-// f[3] prefetched in FP64 (24 B), global id (4 B)
+// smem per footprint node: x[3], v[3], increments[3] (coloured form) as
+// double-word, f[3] prefetched in FP64 (24 B), global id (4 B); the gather
+// form has no increments but one row of gather entries (gw4 x 8 B) per node
+// and a force buffer of 24 double-words per thread
 constexpr int kHexDwNodeBytes = 9 * 8 + 24 + 4;
 
-template <bool SOA>
+// force of element corner i: stress sum_b xi_i[b] t[a][b] minus the hourglass
+// sum_k g_{k,i} q_k[a]
+__device__ __forceinline__ void corner_force(int i, const dw t[3][3], const dw w[4][3], const dw qk[4][3], dw iV,
+                                             dw fa[3])
+{
+    dw gi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int Gk = k == 0 ? sy(i) * sz(i) : (k == 1 ? sx(i) * sz(i) : (k == 2 ? sx(i) * sy(i) : sx(i) * sy(i) * sz(i)));
+        const dw xb = dw_add_fast(dw_add_fast(sgn(w[k][0], sx(i)), sgn(w[k][1], sy(i))), sgn(w[k][2], sz(i)));
+        gi[k] = dw_add_fast(dw{(float)Gk, 0.f}, dw_neg(dw_mul(xb, iV)));
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const dw st = dw_add_fast(dw_add_fast(sgn(t[a][0], sx(i)), sgn(t[a][1], sy(i))), sgn(t[a][2], sz(i)));
+        dw_acc H = dw_dot_begin(gi[0], qk[0][a]);
+        dw_dot_add(H, gi[1], qk[1][a]);
+        dw_dot_add(H, gi[2], qk[2][a]);
+        dw_dot_add(H, gi[3], qk[3][a]);
+        fa[a] = dw_add_fast(st, dw_neg(dw_dot_end(H)));
+    }
+}
+
+template <bool SOA, bool GATHER>
 __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
                                                    const uint4 *__restrict__ lmap, const uint8_t *__restrict__ tcolor,
+                                                   const ushort4 *__restrict__ gat, int gw4,
                                                    const int32_t *__restrict__ fp, const double *__restrict__ x,
                                                    const double *__restrict__ v, const double *__restrict__ sig,
                                                    double *__restrict__ f, double *__restrict__ vol, int64_t nnode,
-                                                   int64_t nelem, int cap, dw kappa, int *__restrict__ err)
+                                                   int64_t nelem, int cap, int cap_f, dw kappa,
+                                                   int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *s_f = reinterpret_cast<double *>(smem_raw);    // [3][cap] FP64
     float2 *s_x = reinterpret_cast<float2 *>(s_f + 3 * cap);  // [3][cap]
     float2 *s_v = s_x + 3 * cap;                           // [3][cap]
-    float2 *s_i = s_v + 3 * cap;                           // [3][cap] increments
-    int *s_gid = reinterpret_cast<int *>(s_i + 3 * cap);
+    float2 *s_i = s_v + 3 * cap;                           // coloured: [3][cap] increments
+    float2 *s_fb = s_i + (GATHER ? 0 : 3 * cap);           // gather: [24][cap_f] corner forces
+    ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_fb + (GATHER ? 24 * cap_f : 0));  // gather: [gw4][cap]
+    int *s_gid = reinterpret_cast<int *>(s_ge + (GATHER ? gw4 * cap : 0));
 
     mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
     const int tid = threadIdx.x;
     const int nn = d.fp_count[0];
     if ((unsigned)(reinterpret_cast<unsigned char *>(s_gid + cap) - smem_raw) > dynamic_smem_bytes() || nn > cap ||
-        d.nitems > (int)blockDim.x) {
+        d.nitems > (int)blockDim.x || (GATHER && ((int)blockDim.x > cap_f || gw4 < 1 || gw4 > 4))) {
         if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
         return;
     }
@@ -68,7 +99,7 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
     int my_color = -1;
     if (active) {
         l = lmap[d.item_start + tid];
-        my_color = tcolor[d.item_start + tid];
+        if (!GATHER) my_color = tcolor[d.item_start + tid];
     }
     for (int i = tid; i < nn; i += blockDim.x) {
         const int64_t g = fpn[i];
@@ -79,7 +110,11 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
             st2(s_v, a * cap + i, dw_from_double_int(v[j]));
             mp_pdl_wait();  // f: written by the previous colour's launch
             s_f[a * cap + i] = f[j];
-            s_i[a * cap + i] = make_float2(0.f, 0.f);
+            if (!GATHER) s_i[a * cap + i] = make_float2(0.f, 0.f);
+        }
+        if (GATHER) {
+            const ushort4 *row = gat + (int64_t)(d.fp_start[0] + i) * gw4;
+            for (int h = 0; h < gw4; ++h) s_ge[h * cap + i] = row[h];
         }
         s_gid[i] = (int)g;
     }
@@ -178,36 +213,58 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
             for (int a = 0; a < 3; ++a) qk[k][a] = dw_mul(dw_dot_end(Q[a]), kappa);
         }
     }
-    for (int c = 0; c < d.ncolors; ++c) {
-        if (my_color == c) {
-#pragma unroll
+    if constexpr (GATHER) {
+        // every thread writes its 24 corner forces at once, then each node
+        // sums the forces of its elements in the block (plan's gather rows)
+        if (active) {
+            // one corner at a time (not unrolled: unrolling spills registers)
+#pragma unroll 1
             for (int i = 0; i < 8; ++i) {
-                dw gi[4];
+                dw fa[3];
+                corner_force(i, t, w, qk, iV, fa);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int Gk = k == 0 ? sy(i) * sz(i)
-                                          : (k == 1 ? sx(i) * sz(i) : (k == 2 ? sx(i) * sy(i) : sx(i) * sy(i) * sz(i)));
-                    const dw xb = dw_add_fast(dw_add_fast(sgn(w[k][0], sx(i)), sgn(w[k][1], sy(i))), sgn(w[k][2], sz(i)));
-                    gi[k] = dw_add_fast(dw{(float)Gk, 0.f}, dw_neg(dw_mul(xb, iV)));
-                }
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    dw fa = dw_add_fast(dw_add_fast(sgn(t[a][0], sx(i)), sgn(t[a][1], sy(i))), sgn(t[a][2], sz(i)));
-                    dw_acc H = dw_dot_begin(gi[0], qk[0][a]);
-                    dw_dot_add(H, gi[1], qk[1][a]);
-                    dw_dot_add(H, gi[2], qk[2][a]);
-                    dw_dot_add(H, gi[3], qk[3][a]);
-                    fa = dw_add_fast(fa, dw_neg(dw_dot_end(H)));
-                    st2(s_i, a * cap + loc[i], dw_add_fast(ld2(s_i, a * cap + loc[i]), fa));
-                }
+                for (int a = 0; a < 3; ++a) st2(s_fb, (3 * i + a) * cap_f + tid, fa[a]);
             }
         }
         __syncthreads();
-    }
-    for (int i = tid; i < nn; i += blockDim.x) {
-        const int64_t g = s_gid[i];
+        for (int i = tid; i < nn; i += blockDim.x) {
+            dw acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            for (int h = 0; h < gw4; ++h) {
+                const ushort4 e4 = s_ge[h * cap + i];
+                const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) f[SOA ? a * nnode + g : 3 * g + a] = f64_add_dw(s_f[a * cap + i], ld2(s_i, a * cap + i));
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned en = es[j];
+                    if (en == 0xFFFFu) continue;
+                    const int te = (int)(en >> 4), corner = (int)(en & 15u);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) acc[a] = dw_add_fast(acc[a], ld2(s_fb, (3 * corner + a) * cap_f + te));
+                }
+            }
+            const int64_t g = s_gid[i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) f[SOA ? a * nnode + g : 3 * g + a] = f64_add_dw(s_f[a * cap + i], acc[a]);
+        }
+    } else {
+        for (int c = 0; c < d.ncolors; ++c) {
+            if (my_color == c) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    dw fa[3];
+                    corner_force(i, t, w, qk, iV, fa);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        st2(s_i, a * cap + loc[i], dw_add_fast(ld2(s_i, a * cap + loc[i]), fa[a]));
+                }
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < nn; i += blockDim.x) {
+            const int64_t g = s_gid[i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                f[SOA ? a * nnode + g : 3 * g + a] = f64_add_dw(s_f[a * cap + i], ld2(s_i, a * cap + i));
+        }
     }
 }
 
@@ -217,8 +274,10 @@ int hex_dw_t(const mp_plan *P, const void *x, const void *v, const void *sig, vo
 {
     if (P->opts.block_size > 256) return MP_EINVAL;
     const int cap = P->stats.footprint_max[0];
-    const int smem = cap * kHexDwNodeBytes;
-    auto kern = hex_hier_dw<SOA>;
+    const bool gather = mp_staged(P, MP_STAGED_GATHER) == MP_STAGED_GATHER && mp_gather_ready(P);
+    const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
+    const int smem = cap * (gather ? kHexDwNodeBytes - 24 : kHexDwNodeBytes) + 24 * 8 * cap_f + 8 * gw4 * cap;
+    auto kern = gather ? hex_hier_dw<SOA, true> : hex_hier_dw<SOA, false>;
     int rc = mp_allow_smem(kern, smem);
     if (rc != MP_OK) return rc;
     int *err = nullptr;
@@ -230,9 +289,10 @@ int hex_dw_t(const mp_plan *P, const void *x, const void *v, const void *sig, vo
         const int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
         if (nb == 0) continue;
         MP_CUDA_TRY(mp_launch(kern, nb, P->opts.block_size, smem, s, overlap, P->dev.desc, b0,
-                              reinterpret_cast<const uint4 *>(P->dev.lmap), P->dev.tcolor, P->dev.fp,
-                              (const double *)x, (const double *)v, (const double *)sig, (double *)f, (double *)vol,
-                              P->maps[0].to_size, P->from_size, cap, kap, err));
+                              reinterpret_cast<const uint4 *>(P->dev.lmap), P->dev.tcolor,
+                              reinterpret_cast<const ushort4 *>(P->dev.gat), gw4, P->dev.fp, (const double *)x,
+                              (const double *)v, (const double *)sig, (double *)f, (double *)vol, P->maps[0].to_size,
+                              P->from_size, cap, cap_f, kap, err));
         overlap = true;
     }
     return MP_OK;

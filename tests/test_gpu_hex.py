@@ -83,10 +83,11 @@ def test_hex_thread_coloured_variant(dtype, staged):
         assert rel_l2(f, fr) <= 1e-5
 
 
-def run_hex_dw(m, sig, v, reorder, layout, block_size=128):
+def run_hex_dw(m, sig, v, reorder, layout, block_size=128, staged=None):
     import paper_1802_03749_gb300 as ml
     from paper_1802_03749_gb300.mesh import HexPlan
-    H = HexPlan(m.nnode, m.elem2node, block_size=block_size, reorder=reorder, coloring="hier", layout=layout)
+    H = HexPlan(m.nnode, m.elem2node, block_size=block_size, reorder=reorder, coloring="hier", layout=layout,
+                staged=staged)
     x = torch.tensor(H.to_plan(m.x, "node"), device="cuda")
     vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
     sd = torch.tensor(H.to_plan(sig, "elem"), device="cuda")
@@ -101,12 +102,23 @@ def run_hex_dw(m, sig, v, reorder, layout, block_size=128):
 @pytest.mark.parametrize("layout", ["aos", "soa"])
 @pytest.mark.parametrize("reorder", ["partition", "rcm"])
 def test_hex_double_word_parity(reorder, layout):
-    """FP64 data with double-word arithmetic: within the FP64 bar."""
+    """FP64 data with double-word arithmetic, gather (default) and
+    thread-coloured increments: within the FP64 bar."""
     m, sig, v = case(14)
-    f, vol = run_hex_dw(m, sig, v, reorder, layout)
     fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
-    assert rel_l2(vol, vr) <= 1e-12
-    assert rel_l2(f, fr) <= 1e-12
+    for staged in (None, "simple"):
+        f, vol = run_hex_dw(m, sig, v, reorder, layout, staged=staged)
+        assert rel_l2(vol, vr) <= 1e-12
+        assert rel_l2(f, fr) <= 1e-12
+
+
+@pytest.mark.parametrize("block_size", [32, 96, 256])
+def test_hex_double_word_gather_ragged_and_deterministic(block_size):
+    m, sig, v = case(11)
+    fr, _ = oracle.hex_force(m.elem2node, m.x, v, sig)
+    a, _ = run_hex_dw(m, sig, v, "partition", "aos", block_size=block_size)
+    b, _ = run_hex_dw(m, sig, v, "partition", "aos", block_size=block_size)
+    assert rel_l2(a, fr) <= 1e-12 and np.array_equal(a, b)
 
 
 @pytest.mark.slow
