@@ -168,11 +168,16 @@ __device__ __forceinline__ dw dw_from_double_int(double d)
     // exponent test in integer arithmetic instead of an FP64 comparison
     unsigned lo32, hi32;
     asm("mov.b64 {%0, %1}, %2;" : "=r"(lo32), "=r"(hi32) : "d"(d));
-    const int e = (int)((hi32 >> 20) & 0x7ffu);
-    if (e < 949 || e > 1150) return dw_from_double_slow(d);  // zero, tiny, huge, inf, nan
+    const unsigned e = (hi32 >> 20) & 0x7ffu;
+    if (e - 949u > 1150u - 949u) return dw_from_double_slow(d);  // zero, tiny, huge, inf, nan
+    // (hi32:lo32) << 3 puts the low 9 exponent bits at 23..31 above the top
+    // 23 significand bits; subtracting 896 << 23 modulo 2^32 leaves the
+    // FP32 exponent e - 896 (53..254 here, so bit 31 ends up clear)
     const unsigned sign = hi32 & 0x80000000u;
-    const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
-    const float scale = __uint_as_float(sign | ((unsigned)(e - 948) << 23));
+    const unsigned hb = (__funnelshift_l(lo32, hi32, 3) - (896u << 23)) | sign;
+    const float h = __uint_as_float(hb);
+    // 2^(e - 948) with the sign: h's exponent lowered by 52
+    const float scale = __uint_as_float(((hb & 0xff800000u) - (52u << 23)));
     const float l = __fmul_rn(__int2float_rn((int)(lo32 & 0x1fffffffu)), scale);
     return dw_fast_two_sum(h, l);
 }
