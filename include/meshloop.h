@@ -261,6 +261,23 @@ int mesh_plan_load(const char *path, mp_plan **out);
 int loop_res_calc(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                   void *res, double gam, double eps, void *stream);
 
+/* res_calc with HOST buffers (pinned host memory for asynchronous copies;
+ * pageable memory works but the copies then block the calling thread).
+ * Arguments and layout as loop_res_calc, all four arrays in host memory.
+ * Enqueues on `stream`, after the work already on it: the copy of x, q,
+ * adt and res into library-owned device buffers (chunks over four internal
+ * copy streams), the loop, and the copy of res back into the caller's array
+ * (chunks over two internal streams), joined back into `stream`.  The result is
+ * in `res` once `stream` has completed; the host arrays must not be
+ * modified before then.  Two device buffer slots (4 arrays each, owned by
+ * the plan, freed with it) alternate between calls, so consecutive calls
+ * issued on two different streams overlap one call's copies with the
+ * other's loop.  Not in the paper: the end-to-end entry point of an
+ * application whose data live on the host.  Errors as loop_res_calc, plus
+ * MP_ECUDA for allocation, stream or copy failures.                       */
+int loop_res_calc_host(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
+                       void *res, double gam, double eps, void *stream);
+
 /* Implementations of the staged two-layer (HIER) loops, chosen per plan
  * with mp_plan_opts.staged:
  *  MP_STAGED_SIMPLE: Algorithm 1 as printed, one block per CTA, increments

@@ -23,7 +23,7 @@ from . import _build
 
 __all__ = [
     "MeshLoopError", "Plan", "lib", "loop_res_calc", "loop_bres_calc", "loop_adt_calc", "loop_save_soln",
-    "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "loop_space_disc", "loop_getacc", "loop_face_flux", "mesh_map_renumber", "mp_check_device_status",
+    "loop_res_calc_host", "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "loop_space_disc", "loop_getacc", "loop_face_flux", "mesh_map_renumber", "mp_check_device_status",
     "REORDER", "COLORING", "LAYOUT", "MP_MAX_BLOCK_COLORS",
 ]
 
@@ -100,6 +100,7 @@ SIGNATURES = {
     "mesh_plan_save": (_I32, [_P, ctypes.c_char_p]),
     "mesh_plan_load": (_I32, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "loop_res_calc": (_I32, [_P, _I32, _P, _P, _P, _P, _D, _D, _P]),
+    "loop_res_calc_host": (_I32, [_P, _I32, _P, _P, _P, _P, _D, _D, _P]),
     "loop_bres_calc": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _D, _D, _P]),
     "loop_adt_calc": (_I32, [_P, _I32, _P, _P, _P, _D, _D, _P]),
     "loop_save_soln": (_I32, [_I64, _I32, _I32, _P, _P, _P]),
@@ -313,6 +314,26 @@ def loop_res_calc(plan: Plan, x, q, adt, res, gam: float = 1.4, eps: float = 0.0
         dt = DTYPE["f64dw"]
     _check(lib().loop_res_calc(plan.handle, dt, _ptr(x), _ptr(q), _ptr(adt), _ptr(res), gam, eps,
                                _stream(stream)), "loop_res_calc")
+
+
+def loop_res_calc_host(plan: Plan, x, q, adt, res, gam: float = 1.4, eps: float = 0.05, stream=None,
+                       compute: str | None = None):
+    """res_calc on HOST tensors (pinned for asynchronous copies): the library
+    copies x, q, adt, res in, runs the loop and copies res back, on
+    ``stream``; the result is in ``res`` once the stream has completed."""
+    import torch
+    dt = x.dtype
+    for t in (x, q, adt, res):
+        if t.dtype != dt or t.is_cuda or not t.is_contiguous():
+            raise MeshLoopError(-1, "tensors must be contiguous host tensors of one dtype")
+    if dt == torch.float64:
+        code = DTYPE["f64dw"] if compute == "dw" else DTYPE["f64"]
+    elif dt == torch.float32 and compute is None:
+        code = DTYPE["f32"]
+    else:
+        raise MeshLoopError(-1, f"unsupported dtype {dt} / compute {compute}")
+    _check(lib().loop_res_calc_host(plan.handle, code, _ptr(x), _ptr(q), _ptr(adt), _ptr(res), gam, eps,
+                                    _stream(stream)), "loop_res_calc_host")
 
 
 def loop_bres_calc(plan: Plan, x, q, adt, res, qinf, gam: float = 1.4, eps: float = 0.05, stream=None):

@@ -109,6 +109,8 @@ int mp_device_error_word(int **word);
 
 // Uploads the plan's tables to the current device if not done yet.
 int mp_plan_ensure_device(const mp_plan *plan);
+// releases what loop_res_calc_host keeps on the plan (host_io.cu)
+void mp_host_io_free(void *io);
 
 // Pipelined persistent two-layer res_calc (FP64 / FP32).
 int mp_res_calc_pipe(const mp_plan *P, int32_t dtype, const void *x, const void *q, const void *adt, void *res,

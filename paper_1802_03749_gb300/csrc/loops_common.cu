@@ -37,6 +37,7 @@ void mp_plan_free_device(mp_plan *P)
     cudaFree(d.inv_off);
     cudaFree(d.inv_idx);
     cudaFree(d.scratch);
+    mp_host_io_free(d.host_io);
     if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
     d = mp_device_tables{};
 }

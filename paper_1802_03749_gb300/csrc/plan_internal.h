@@ -37,6 +37,7 @@ struct mp_device_tables {
     int32_t *inv_idx = nullptr;  // TWOSTEP: item * arity + slot, sorted by (point, item, slot)
     void *scratch = nullptr;     // TWOSTEP: per-(item, slot) increments
     size_t scratch_bytes = 0;
+    void *host_io = nullptr;     // loop_res_calc_host: device buffers, copy streams (host_io.cu)
     int64_t bytes = 0;
 };
 
