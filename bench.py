@@ -224,8 +224,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gedges/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, FP64", "cells": m.ncell,
-                       "edges": m.nedge},
+            "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, FP64 data",
+                       "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge,
+                       "implementation": "sequential FP64 CPU oracle (edge loop in mesh order), 1 host core"},
             "cpu_baseline": {"value": v, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full res_calc passes of {m.nedge} edges, 1 host core"},
             "e2e": {"value": v, "unit": "Gedges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -705,13 +706,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, "
-                                   + ("FP32 data" if f32 else "FP64 data")
-                                   + (", double-word arithmetic" if compute else "")
-                                   + f", two-layer colouring"
-                                   + f" ({'thread-coloured' if head_staged == 'simple' else head_staged} increments)"
-                                   + f", RCM + partition, block {args.block_size}, "
-                                   + args.layout.upper(),
-                       "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge, "parallelism": f"replicas x{world}",
+                                   + ("FP32 data" if f32 else "FP64 data"),
+                       "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge,
+                       "implementation": ("double-word arithmetic, " if compute else "")
+                                         + f"two-layer colouring"
+                                         + f" ({'thread-coloured' if head_staged == 'simple' else head_staged}"
+                                         + f" increments), RCM + partition, block {args.block_size}, "
+                                         + args.layout.upper(),
+                       "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (useful bytes {useful / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB)"},
             "useful_gbs": gbs, "useful_frac_hbm": gbs / hbm_peak,
             "roofline": roof, "cpu_baseline": cpu,
