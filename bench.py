@@ -344,13 +344,16 @@ def bench_increment(ml, torch, timer, args):
     from paper_1802_03749_gb300.mesh import ScatterPlan
     hbm, _ = read_peaks()
     rows = {}
-    variants = (("hier", "partition", "gather"), ("hier", "partition", "simple"), ("hier", "rcm", "gather"),
-                ("global", "rcm", None), ("atomic", "rcm", None), ("atomic", "none", None))
+    variants = (("hier", "partition", "gather", "aos"), ("hier", "partition", "gather", "soa"),
+                ("hier", "partition", "simple", "aos"), ("hier", "rcm", "gather", "aos"),
+                ("global", "rcm", None, "aos"), ("atomic", "rcm", None, "aos"), ("atomic", "rcm", None, "soa"),
+                ("atomic", "none", None, "aos"))
     tm = meshgen.tri_mesh(1100, 1100)
     ed, ia = meshgen.volna_fields(tm)
     ub = tm.nedge * (7 * 4 + 4 + 2 * 4) + tm.ncell * (4 + 2 * 16)
-    for coloring, reorder, staged in variants:
-        S = ScatterPlan(tm.ncell, tm.edge2cell, block_size=256, reorder=reorder, coloring=coloring, staged=staged)
+    for coloring, reorder, staged, layout in variants:
+        S = ScatterPlan(tm.ncell, tm.edge2cell, block_size=256, reorder=reorder, coloring=coloring, staged=staged,
+                        layout=layout)
         S.plan.upload()
         t = lambda a, w: torch.tensor(S.to_plan(a, w), dtype=torch.float32, device="cuda")
         edd, iad = t(ed, "from"), t(ia, "to")
@@ -358,7 +361,7 @@ def bench_increment(ml, torch, timer, args):
         res = torch.zeros((tm.ncell, 4), dtype=torch.float32, device="cuda")
         ms, _ = timer(lambda: ml.loop_space_disc(S.plan, edd, fl, iad, res), 20, 3)
         st = S.plan.stats()
-        rows[f"space_disc_f32_{coloring}_{reorder}" + (f"_{staged}" if staged else "")] = {
+        rows[f"space_disc_f32_{coloring}_{reorder}" + (f"_{staged}" if staged else "") + f"_{layout}"] = {
             "workload": f"Volna-style edge loop, {tm.ncell} triangles, {tm.nedge} edges, FP32", "ms": ms,
             "gedges_s": tm.nedge / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
             "block_colors": st["nblock_colors"], "reuse": st["reuse_all"]}
@@ -367,14 +370,15 @@ def bench_increment(ml, torch, timer, args):
     qm = meshgen.quad_mesh(2000, 2000)
     cd = meshgen.bookleaf_fields(qm.ncell)
     ub = qm.ncell * (17 * 8 + 4 * 4) + qm.nnode * 2 * 32
-    for coloring, reorder, staged in variants:
-        S = ScatterPlan(qm.nnode, qm.cell2node, block_size=256, reorder=reorder, coloring=coloring, staged=staged)
+    for coloring, reorder, staged, layout in variants:
+        S = ScatterPlan(qm.nnode, qm.cell2node, block_size=256, reorder=reorder, coloring=coloring, staged=staged,
+                        layout=layout)
         S.plan.upload()
         cdd = torch.tensor(S.to_plan(cd, "from"), device="cuda")
         nd = torch.zeros((qm.nnode, 4), dtype=torch.float64, device="cuda")
         ms, _ = timer(lambda: ml.loop_getacc(S.plan, cdd, nd), 20, 3)
         st = S.plan.stats()
-        rows[f"getacc_f64_{coloring}_{reorder}" + (f"_{staged}" if staged else "")] = {
+        rows[f"getacc_f64_{coloring}_{reorder}" + (f"_{staged}" if staged else "") + f"_{layout}"] = {
             "workload": f"BookLeaf-style cell loop, {qm.ncell} quads, FP64", "ms": ms,
             "gcells_s": qm.ncell / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
             "block_colors": st["nblock_colors"], "reuse": st["reuse_all"]}
