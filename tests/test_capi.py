@@ -57,3 +57,39 @@ def test_error_strings():
     import paper_1802_03749_gb300 as ml
     for code in range(0, -10, -1):
         assert ml.lib().mp_error_string(code)
+
+
+def test_loop_argument_errors_without_device():
+    """Every loop entry point rejects bad arguments before touching a
+    device: null data pointers and unknown dtypes give MP_EINVAL, a plan of
+    the wrong shape MP_EPLAN (no GPU needed)."""
+    import ctypes
+    import paper_1802_03749_gb300 as ml
+    L = ml.lib()
+    EINVAL, EPLAN = -1, -8
+    assert ml.lib().mp_error_string(EINVAL) and ml.lib().mp_error_string(EPLAN)
+    q = meshgen.quad_mesh(6, 4, seed=2)
+    res_plan = ml.Plan([{"to_set": 1, "idx": q.edge2node, "to_size": q.nnode},
+                        {"to_set": 2, "idx": q.edge2cell, "to_size": q.ncell, "written": True}], q.nedge,
+                       block_size=32)
+    cell_plan = ml.Plan([{"to_set": 1, "idx": q.cell2node, "to_size": q.nnode, "written": True}], q.ncell,
+                        block_size=32)
+    edge_plan = ml.Plan([{"to_set": 1, "idx": q.edge2cell, "to_size": q.ncell, "written": True}], q.nedge,
+                        block_size=32)
+    N = None
+    F64, BAD = 0, 7
+    # res_calc on device and host arrays
+    assert L.loop_res_calc(res_plan.handle, BAD, N, N, N, N, 1.4, 0.05, N) == EINVAL
+    assert L.loop_res_calc_host(res_plan.handle, F64, N, N, N, N, 1.4, 0.05, N) == EINVAL
+    assert L.loop_res_calc_host(None, F64, N, N, N, N, 1.4, 0.05, N) == EINVAL
+    # increment-only loops and the face flux: null pointers, then wrong plans
+    assert L.loop_space_disc(edge_plan.handle, F64, N, N, N, N, N) == EINVAL
+    assert L.loop_space_disc(cell_plan.handle, F64, N, N, N, N, N) == EPLAN
+    assert L.loop_getacc(cell_plan.handle, F64, N, N, N) == EINVAL
+    assert L.loop_getacc(edge_plan.handle, F64, N, N, N) == EPLAN
+    assert L.loop_face_flux(edge_plan.handle, F64, N, N, N, 1.4, 1e-3, 0.72, N) == EINVAL
+    assert L.loop_face_flux(edge_plan.handle, F64, N, N, N, 1.0, 1e-3, 0.72, N) == EINVAL   # gamma must exceed 1
+    assert L.loop_face_flux(cell_plan.handle, F64, N, N, N, 1.4, 1e-3, 0.72, N) == EPLAN
+    assert L.loop_elem_assemble(res_plan.handle, F64, N, N, N, N, N, 0.01, N) == EPLAN
+    assert L.mesh_plan_set_staged(res_plan.handle, 7) == EINVAL
+    assert L.mesh_plan_set_staged(res_plan.handle, 6) == 0
