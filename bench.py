@@ -347,7 +347,7 @@ def bench_increment(ml, torch, timer, args):
     variants = (("hier", "partition", "gather", "aos"), ("hier", "partition", "gather", "soa"),
                 ("hier", "partition", "simple", "aos"), ("hier", "rcm", "gather", "aos"),
                 ("global", "rcm", None, "aos"), ("atomic", "rcm", None, "aos"), ("atomic", "rcm", None, "soa"),
-                ("atomic", "none", None, "aos"))
+                ("atomic", "none", None, "aos"), ("twostep", "rcm", None, "aos"), ("twostep", "rcm", None, "soa"))
     tm = meshgen.tri_mesh(1100, 1100)
     ed, ia = meshgen.volna_fields(tm)
     ub = tm.nedge * (7 * 4 + 4 + 2 * 4) + tm.ncell * (4 + 2 * 16)

@@ -389,12 +389,15 @@ int loop_adjoint(const mp_plan *plan, int32_t dtype, const void *x, const void *
  *   res[c1] -= inv_area[c1] w;  res[c2] += inv_area[c2] w  unless eflag = 1
  * (a boundary edge lists its one cell twice and has eflag 1).
  * Plan: maps {edge->cell (2, written)}; HIER (gather increments by
- * default, MP_STAGED_SIMPLE for thread colours), GLOBAL or ATOMIC.  dtype MP_F32
+ * default, MP_STAGED_SIMPLE for thread colours), GLOBAL, ATOMIC or TWOSTEP
+ * (owner computes: one launch over the cells, each summing its edges'
+ * increments recomputed from their direct data through the plan's inverse
+ * map; no temporary array, no atomics, deterministic).  dtype MP_F32
  * (the paper's precision for this loop) or MP_F64.  edata [edges][7] (SoA
  * [7][edges]), eflag int32 [edges], inv_area [cells], res [cells][4] (SoA
  * [4][cells]); all device memory in plan numbering, 16-byte aligned.
  * Errors: MP_EINVAL (dtype, null or misaligned pointer), MP_EPLAN (plan
- * shape or TWOSTEP colouring), MP_ECUDA.                                  */
+ * shape), MP_ECUDA.                                                      */
 int loop_space_disc(const mp_plan *plan, int32_t dtype, const void *edata, const int32_t *eflag,
                     const void *inv_area, void *res, void *stream);
 
@@ -403,8 +406,8 @@ int loop_space_disc(const mp_plan *plan, int32_t dtype, const void *edata, const
  * (rho, m[4], w[4], fx[4], fy[4]); node k of the cell (cell->node order) gets
  *   nd[n_k] += (m_k, rho w_k, fx_k, fy_k).
  * Plan: maps {cell->node (4, written)}; HIER (block size <= 512; gather
- * increments by default, MP_STAGED_SIMPLE for thread colours), GLOBAL or
- * ATOMIC.  dtype MP_F64 (the paper's precision) or MP_F32.  cdata
+ * increments by default, MP_STAGED_SIMPLE for thread colours), GLOBAL,
+ * ATOMIC or TWOSTEP (owner computes, as loop_space_disc).  dtype MP_F64 (the paper's precision) or MP_F32.  cdata
  * [cells][17] (SoA [17][cells]), nd [nodes][4] (SoA [4][nodes]); device
  * memory in plan numbering, 16-byte aligned.  Errors as loop_space_disc. */
 int loop_getacc(const mp_plan *plan, int32_t dtype, const void *cdata, void *nd, void *stream);

@@ -15,7 +15,7 @@
 // The staged (HIER) kernels stage only the written set: its current values
 // (prefetched, so the write-back is a plain store) and, for space_disc, the
 // one value read per cell.  The direct data are read once, by their own
-// thread.  Increments: gather (the default: each thread stores its
+// thread.  TWOSTEP plans run the owner-computes form below.  Increments: gather (the default: each thread stores its
 // increments in shared memory, one barrier, every footprint point sums them
 // through the plan's block-local inverse map) or thread colours (Algorithm
 // 1, MP_STAGED_SIMPLE).  GLOBAL plans run one launch per colour with plain
@@ -339,6 +339,60 @@ __global__ void __launch_bounds__(256) getacc_direct(int c0, int c1, const int32
     }
 }
 
+// ------------------------------------------------- owner-computes (TWOSTEP)
+// The two-step method (Sec. 2.1) stores every increment in a temporary array
+// and then gathers it per point through the inverse map.  The increments of
+// these two loops are cheap functions of their iteration's direct data, so
+// here each point recomputes them while it gathers: one launch over the
+// written set, no temporary array, no atomics, fixed order (deterministic).
+
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(256) space_disc_owner(const int32_t *__restrict__ inv_off,
+                                                        const int32_t *__restrict__ inv_idx, const T *__restrict__ ed,
+                                                        const int32_t *__restrict__ eflag,
+                                                        const T *__restrict__ inv_area, T *__restrict__ res,
+                                                        int64_t nedge, int64_t ncell)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    T a[4] = {T(0), T(0), T(0), T(0)};
+    for (int j = inv_off[c]; j < inv_off[c + 1]; ++j) {
+        const int en = inv_idx[j];
+        const int64_t e = en >> 1;
+        const bool second = en & 1;
+        if (second && eflag[e]) continue;
+        T w[4];
+        space_disc_w<T, SOA>(ed, nedge, e, w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = second ? a[k] + w[k] : a[k] - w[k];
+    }
+    const T ia = inv_area[c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) *res_at<T, SOA>(res, ncell, c, k) += ia * a[k];
+}
+
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(256) getacc_owner(const int32_t *__restrict__ inv_off,
+                                                    const int32_t *__restrict__ inv_idx, const T *__restrict__ cd,
+                                                    T *__restrict__ nd, int64_t ncell, int64_t nnode)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnode) return;
+    T a[4] = {T(0), T(0), T(0), T(0)};
+    for (int j = inv_off[p]; j < inv_off[p + 1]; ++j) {
+        const int en = inv_idx[j];
+        const int64_t c = en >> 2;
+        const int k = en & 3;
+        auto at = [&](int f) { return SOA ? cd[f * ncell + c] : cd[17 * c + f]; };
+        a[0] += at(1 + k);
+        a[1] += at(0) * at(5 + k);
+        a[2] += at(9 + k);
+        a[3] += at(13 + k);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) (SOA ? nd[k * nnode + p] : nd[4 * p + k]) += a[k];
+}
+
 // ----------------------------------------------------------------- drivers
 
 template <typename T, bool SOA>
@@ -366,6 +420,11 @@ int space_disc_t(const mp_plan *P, const void *ed, const int32_t *eflag, const v
                                   eflag, (const T *)ia, (T *)res, nedge, ncell, cap, cap_f, err));
             overlap = true;
         }
+        return MP_OK;
+    }
+    if (co == MP_COLOR_TWOSTEP) {
+        MP_CUDA_TRY(mp_launch(space_disc_owner<T, SOA>, (int)((ncell + 255) / 256), 256, 0, s, false, P->dev.inv_off,
+                              P->dev.inv_idx, (const T *)ed, eflag, (const T *)ia, (T *)res, nedge, ncell));
         return MP_OK;
     }
     if (co != MP_COLOR_GLOBAL && co != MP_COLOR_ATOMIC) return MP_EPLAN;
@@ -410,6 +469,11 @@ int getacc_t(const mp_plan *P, const void *cd, void *nd, cudaStream_t s)
         }
         return MP_OK;
     }
+    if (co == MP_COLOR_TWOSTEP) {
+        MP_CUDA_TRY(mp_launch(getacc_owner<T, SOA>, (int)((nnode + 255) / 256), 256, 0, s, false, P->dev.inv_off,
+                              P->dev.inv_idx, (const T *)cd, (T *)nd, ncell, nnode));
+        return MP_OK;
+    }
     if (co != MP_COLOR_GLOBAL && co != MP_COLOR_ATOMIC) return MP_EPLAN;
     const bool atomic = co == MP_COLOR_ATOMIC;
     bool overlap = false;
@@ -438,7 +502,6 @@ extern "C" int loop_space_disc(const mp_plan *P, int32_t dtype, const void *edat
 {
     if (!P || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
     if (P->nmaps != 1 || P->maps[0].arity != 2 || !P->maps[0].written) return MP_EPLAN;
-    if (P->opts.coloring == MP_COLOR_TWOSTEP) return MP_EPLAN;
     if (P->from_size == 0) return MP_OK;
     if (!ok_ptrs({edata, eflag, inv_area, res})) return MP_EINVAL;
     int rc = mp_plan_ensure_device(P);
@@ -460,7 +523,6 @@ extern "C" int loop_getacc(const mp_plan *P, int32_t dtype, const void *cdata, v
 {
     if (!P || (dtype != MP_F64 && dtype != MP_F32)) return MP_EINVAL;
     if (P->nmaps != 1 || P->maps[0].arity != 4 || !P->maps[0].written) return MP_EPLAN;
-    if (P->opts.coloring == MP_COLOR_TWOSTEP) return MP_EPLAN;
     if (P->from_size == 0) return MP_OK;
     if (!ok_ptrs({cdata, nd})) return MP_EINVAL;
     int rc = mp_plan_ensure_device(P);

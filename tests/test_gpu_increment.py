@@ -2,8 +2,9 @@
 the C ABI: the Volna-style edge loop (FP32, the paper's precision, and
 FP64) and the BookLeaf-style cell loop (FP64, the paper's precision, and
 FP32), with staged two-layer (thread-coloured and gather increments),
-global-colour and atomic plans.  FP64 rel-L2 <= 1e-12; FP32 <= 1e-5 against
-the oracle fed the same FP32-rounded inputs."""
+global-colour, atomic and owner-computes (two-step) plans.  FP64 rel-L2
+<= 1e-12; FP32 <= 1e-5 against the oracle fed the same FP32-rounded
+inputs."""
 import numpy as np
 import pytest
 
@@ -16,7 +17,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 VARIANTS = [("hier", "partition", None), ("hier", "partition", "simple"), ("hier", "rcm", None),
-            ("global", "rcm", None), ("atomic", "rcm", None), ("atomic", "none", None)]
+            ("global", "rcm", None), ("atomic", "rcm", None), ("atomic", "none", None), ("twostep", "rcm", None),
+            ("twostep", "none", None)]
 
 
 @pytest.fixture(scope="module")
