@@ -97,7 +97,7 @@ __device__ __forceinline__ void dw_side(const float2 *s, int cap, int c, const d
 //   float2 staged[29][cap], inc[5][cap]
 //   int    gid[cap]
 template <bool SOA>
-__global__ void __launch_bounds__(128) face_flux_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
+__global__ void __launch_bounds__(128, 5) face_flux_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
                                                          const ushort4 *__restrict__ lmap,
                                                          const uint8_t *__restrict__ tcolor,
                                                          const int32_t *__restrict__ fp,
