@@ -623,6 +623,8 @@ def main():
     roof["traffic"] = headline_traffic(args, head_staged)
     roof["traffic_scope"] = "DRAM bytes per pass (all block-colour launches), as achieved; ncu capture"
     roof["useful_bytes"] = useful
+    # the data reuse measure of the plan: useful bytes / DRAM bytes per pass
+    roof["useful_over_dram"] = useful / roof["traffic"] if roof["traffic"] else None
 
     # ---------------------------------------------------------- e2e (host buffers)
     # through the C-ABI call with host arrays (loop_res_calc_host): every step
