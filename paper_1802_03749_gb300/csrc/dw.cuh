@@ -111,6 +111,24 @@ __device__ __forceinline__ void dw_dot_add(dw_acc &A, dw a, dw b)
 
 __device__ __forceinline__ dw dw_dot_end(dw_acc A) { return dw_fast_two_sum(A.s, A.c); }
 
+// Compensated sum of double-words (the Sum2 scheme of the same paper with
+// double-word terms): the high parts are summed with TwoSum, the TwoSum
+// errors and the low parts gathered in one float, added back with TwoSum
+// at the end (the sum may cancel, so FastTwoSum's ordering is not assumed).
+// The term is sg * x for sg in {-1, 0, 1}: the products are exact, so the
+// FMAs below round exactly where TwoSum of (S.s, sg x.hi) would.  8 FP32
+// operations per term instead of 11 for a sloppy double-word addition.
+__device__ __forceinline__ void dw_sum_add(dw_acc &S, dw x, float sg)
+{
+    const float s = __fmaf_rn(sg, x.hi, S.s);
+    const float bb = __fsub_rn(s, S.s);
+    const float e = __fadd_rn(__fsub_rn(S.s, __fsub_rn(s, bb)), __fmaf_rn(sg, x.hi, -bb));
+    S.s = s;
+    S.c = __fadd_rn(S.c, __fmaf_rn(sg, x.lo, e));
+}
+
+__device__ __forceinline__ dw dw_sum_end(dw_acc S) { return dw_two_sum(S.s, S.c); }
+
 // x * 2^k for a power of two (exact)
 __device__ __forceinline__ dw dw_scale2(dw x, float p2) { return {__fmul_rn(x.hi, p2), __fmul_rn(x.lo, p2)}; }
 

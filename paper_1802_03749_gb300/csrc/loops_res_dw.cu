@@ -227,23 +227,26 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         // each cell sums its edges' fluxes: +f from the edge's first cell
         // slot (map slot 2), -f from its second (slot 3)
         for (int i = tid; i < nc; i += blockDim.x) {
-            dw a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            // branch-free: a padding entry adds 0 times slot 0 (thread 0's
+            // flux, computed in every block)
+            dw_acc S[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (int h = 0; h < gw4; ++h) {
                 const ushort4 e4 = s_ge[h * cap_c + i];
                 const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const unsigned e = es[j];
-                    if (e == 0xFFFFu) continue;
-                    const int t = (int)(e >> 4);
-                    const bool neg = (e & 15u) == 3u;
+                    const bool valid = e != 0xFFFFu;
+                    const int t = valid ? (int)(e >> 4) : 0;
+                    const float sg = !valid ? 0.0f : ((e & 15u) == 3u ? -1.0f : 1.0f);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const dw v = ld(s_inc, k * cap_f + t);
-                        a[k] = dw_add_fast(a[k], neg ? dw_neg(v) : v);
+                        dw_sum_add(S[k], v, sg);
                     }
                 }
             }
+            const dw a[4] = {dw_sum_end(S[0]), dw_sum_end(S[1]), dw_sum_end(S[2]), dw_sum_end(S[3])};
             const int64_t g = s_gid[i];
             if (SOA) {
 #pragma unroll
