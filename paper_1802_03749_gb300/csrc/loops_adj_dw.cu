@@ -225,48 +225,48 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         }
         __syncthreads();
         // cells: q_bar of the edges' first (map slot 2) or second (slot 3) cell
+        // (compensated double-word sums, branch-free: a padding entry adds 0
+        // times the values of thread 0, computed in every block)
         for (int i = tid; i < nc; i += blockDim.x) {
-            dw a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            dw_acc S[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (int h = 0; h < gw4; ++h) {
                 const ushort4 e4 = s_ge[h * cap_c + i];
                 const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const unsigned en = es[j];
-                    if (en == 0xFFFFu) continue;
-                    const int t = (int)(en >> 4), base = (en & 15u) == 3u ? 4 : 0;
+                    const bool valid = en != 0xFFFFu;
+                    const int t = valid ? (int)(en >> 4) : 0, base = (en & 15u) == 3u ? 4 : 0;
+                    const float sg = valid ? 1.0f : 0.0f;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) a[k] = dw_add_fast(a[k], ldw(s_fb, (base + k) * cap_f + t));
+                    for (int k = 0; k < 4; ++k) dw_sum_add(S[k], ldw(s_fb, (base + k) * cap_f + t), sg);
                 }
             }
             const int64_t g = s_gc[i];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) qbar[SOA ? k * ncell + g : 4 * g + k] = f64_add_dw(s_qb[k * cap_c + i], a[k]);
+            for (int k = 0; k < 4; ++k)
+                qbar[SOA ? k * ncell + g : 4 * g + k] = f64_add_dw(s_qb[k * cap_c + i], dw_sum_end(S[k]));
         }
         // nodes: node a (slot 0) gets (-n_y_bar, n_x_bar), node b (slot 1) the opposite
         for (int i = tid; i < nn; i += blockDim.x) {
-            dw ax = {0.f, 0.f}, ay = {0.f, 0.f};
+            dw_acc Sx = {0.f, 0.f}, Sy = {0.f, 0.f};
             for (int h = 0; h < gw4; ++h) {
                 const ushort4 e4 = s_ge[gw4 * cap_c + h * cap_n + i];
                 const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const unsigned en = es[j];
-                    if (en == 0xFFFFu) continue;
-                    const int t = (int)(en >> 4);
+                    const bool valid = en != 0xFFFFu;
+                    const int t = valid ? (int)(en >> 4) : 0;
+                    const float sg = !valid ? 0.0f : ((en & 15u) == 0u ? 1.0f : -1.0f);
                     const dw bx = ldw(s_fb, 8 * cap_f + t), by = ldw(s_fb, 9 * cap_f + t);
-                    if ((en & 15u) == 0u) {
-                        ax = dw_add_fast(ax, dw_neg(by));
-                        ay = dw_add_fast(ay, bx);
-                    } else {
-                        ax = dw_add_fast(ax, by);
-                        ay = dw_add_fast(ay, dw_neg(bx));
-                    }
+                    dw_sum_add(Sx, by, -sg);
+                    dw_sum_add(Sy, bx, sg);
                 }
             }
             const int64_t g = s_gn[i];
-            xbar[SOA ? g : 2 * g] = f64_add_dw(s_xb[i], ax);
-            xbar[SOA ? nnode + g : 2 * g + 1] = f64_add_dw(s_xb[cap_n + i], ay);
+            xbar[SOA ? g : 2 * g] = f64_add_dw(s_xb[i], dw_sum_end(Sx));
+            xbar[SOA ? nnode + g : 2 * g + 1] = f64_add_dw(s_xb[cap_n + i], dw_sum_end(Sy));
         }
     } else {
     for (int c = 0; c < d.ncolors; ++c) {

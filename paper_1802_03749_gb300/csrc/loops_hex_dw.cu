@@ -227,23 +227,27 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
             }
         }
         __syncthreads();
+        // compensated double-word sums, branch-free: a padding entry adds 0
+        // times corner 0 of thread 0 (computed in every block)
         for (int i = tid; i < nn; i += blockDim.x) {
-            dw acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            dw_acc S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (int h = 0; h < gw4; ++h) {
                 const ushort4 e4 = s_ge[h * cap + i];
                 const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const unsigned en = es[j];
-                    if (en == 0xFFFFu) continue;
-                    const int te = (int)(en >> 4), corner = (int)(en & 15u);
+                    const bool valid = en != 0xFFFFu;
+                    const int te = valid ? (int)(en >> 4) : 0, corner = valid ? (int)(en & 15u) : 0;
+                    const float sg = valid ? 1.0f : 0.0f;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) acc[a] = dw_add_fast(acc[a], ld2(s_fb, (3 * corner + a) * cap_f + te));
+                    for (int a = 0; a < 3; ++a) dw_sum_add(S[a], ld2(s_fb, (3 * corner + a) * cap_f + te), sg);
                 }
             }
             const int64_t g = s_gid[i];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) f[SOA ? a * nnode + g : 3 * g + a] = f64_add_dw(s_f[a * cap + i], acc[a]);
+            for (int a = 0; a < 3; ++a)
+                f[SOA ? a * nnode + g : 3 * g + a] = f64_add_dw(s_f[a * cap + i], dw_sum_end(S[a]));
         }
     } else {
         for (int c = 0; c < d.ncolors; ++c) {
