@@ -31,9 +31,10 @@ namespace {
 // Dynamic shared memory for cap_c cells and cap_n nodes:
 //   double x, y                                    (16 B per node)
 //   double res[4]  (prefetched at staging)         (32 B per cell)
-//   dw   rho, ru, rv, E, eps adt/2, u, v, p, H     (9 x 8 B per cell)
+//   dw   [cap_c][9]: rho, ru, rv, E, eps adt/2, u, v, p, H of each cell
+//                        (72 B per cell)
 //   dw   inc[4][cap_c]   coloured form             (32 B per cell)
-//        f[4][cap_f]     gather form: over the primitives, extended when
+//        f[4][cap_f]     gather form: over the records, extended when
 //                        4 cap_f > 9 cap_c
 //   int  gid                                       (4 B per cell)
 //   ushort4 ge[gw4][cap_c]  gather form            (8 gw4 B per cell)
@@ -64,19 +65,21 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
     double *s_x = reinterpret_cast<double *>(smem_raw);
     double *s_y = s_x + cap_n;
     double *s_res = s_y + cap_n;  // [4][cap_c]
+    // per-cell records of 9 double-words, [cap_c][9]: an odd stride in
+    // 8-byte words keeps 16 consecutive cells on distinct bank pairs
     float2 *s_r = reinterpret_cast<float2 *>(s_res + 4 * cap_c);
-    float2 *s_ru = s_r + cap_c;
-    float2 *s_rv = s_ru + cap_c;
-    float2 *s_E = s_rv + cap_c;
-    float2 *s_a = s_E + cap_c;
-    float2 *s_u = s_a + cap_c;
-    float2 *s_v = s_u + cap_c;
-    float2 *s_p = s_v + cap_c;
-    float2 *s_H = s_p + cap_c;
+    float2 *s_ru = s_r + 1;
+    float2 *s_rv = s_r + 2;
+    float2 *s_E = s_r + 3;
+    float2 *s_a = s_r + 4;
+    float2 *s_u = s_r + 5;
+    float2 *s_v = s_r + 6;
+    float2 *s_p = s_r + 7;
+    float2 *s_H = s_r + 8;
     // increments [4][cap_c] (coloured) after the primitives; the gather
     // form's fluxes [4][cap_f] overwrite the primitives once all threads
     // have read them
-    float2 *s_inc = GATHER ? s_r : s_H + cap_c;
+    float2 *s_inc = GATHER ? s_r : s_r + 9 * cap_c;
     float2 *s_tail = GATHER ? s_r + max(9 * cap_c, 4 * cap_f) : s_inc + 4 * cap_c;
     ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_tail);  // [gw4][cap_c]
     int *s_gid = reinterpret_cast<int *>(s_ge + (GATHER ? gw4 * cap_c : 0));
@@ -136,15 +139,15 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         dw u = dw_mul(RU, ri), v = dw_mul(RV, ri);
         dw kin = dw_scale2(dw_add_fast(dw_mul(RU, u), dw_mul(RV, v)), 0.5f);
         dw p = dw_mul(gm1, dw_add_fast(EE, dw_neg(kin)));
-        st(s_r, i, R);
-        st(s_ru, i, RU);
-        st(s_rv, i, RV);
-        st(s_E, i, EE);
-        st(s_a, i, dw_mul(dw_from_double_int(adt[g]), half_eps));  // eps adt / 2
-        st(s_u, i, u);
-        st(s_v, i, v);
-        st(s_p, i, p);
-        st(s_H, i, dw_add_fast(EE, p));
+        st(s_r, 9 * i, R);
+        st(s_ru, 9 * i, RU);
+        st(s_rv, 9 * i, RV);
+        st(s_E, 9 * i, EE);
+        st(s_a, 9 * i, dw_mul(dw_from_double_int(adt[g]), half_eps));  // eps adt / 2
+        st(s_u, 9 * i, u);
+        st(s_v, 9 * i, v);
+        st(s_p, 9 * i, p);
+        st(s_H, 9 * i, dw_add_fast(EE, p));
         if (GATHER) {
             const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
             for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];
@@ -176,22 +179,23 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         // n = (y_a - y_b, x_b - x_a), exact in FP64 for nearby nodes; halved
         const dw nxh = dw_scale2(dw_from_double_int(s_y[na] - s_y[nb]), 0.5f);
         const dw nyh = dw_scale2(dw_from_double_int(s_x[nb] - s_x[na]), 0.5f);
-        const dw r1 = ld(s_r, c1), r2 = ld(s_r, c2);
-        const dw ru1 = ld(s_ru, c1), ru2 = ld(s_ru, c2);
-        const dw rv1 = ld(s_rv, c1), rv2 = ld(s_rv, c2);
-        const dw p1 = ld(s_p, c1), p2 = ld(s_p, c2);
+        const dw r1 = ld(s_r, 9 * c1), r2 = ld(s_r, 9 * c2);
+        const dw ru1 = ld(s_ru, 9 * c1), ru2 = ld(s_ru, 9 * c2);
+        const dw rv1 = ld(s_rv, 9 * c1), rv2 = ld(s_rv, 9 * c2);
+        // p1 + p2: two positive pressures, no cancellation
+        const dw pp = dw_add_fast(ld(s_p, 9 * c1), ld(s_p, 9 * c2));
         // each component is one compensated sum of products:
         //   V = u nx/2 + v ny/2,  mu = eps (adt1 + adt2) / 2,
         //   f0 = r1 V1 + r2 V2 + mu r1 - mu r2
-        //   f1 = ru1 V1 + ru2 V2 + p1 nx/2 + p2 nx/2 + mu ru1 - mu ru2   (f2 likewise)
+        //   f1 = ru1 V1 + ru2 V2 + (p1 + p2) nx/2 + mu ru1 - mu ru2   (f2 likewise)
         //   f3 = H1 V1 + H2 V2 + mu E1 - mu E2
-        dw_acc A = dw_dot_begin(ld(s_u, c1), nxh);
-        dw_dot_add(A, ld(s_v, c1), nyh);
+        dw_acc A = dw_dot_begin(ld(s_u, 9 * c1), nxh);
+        dw_dot_add(A, ld(s_v, 9 * c1), nyh);
         const dw V1 = dw_dot_end(A);
-        A = dw_dot_begin(ld(s_u, c2), nxh);
-        dw_dot_add(A, ld(s_v, c2), nyh);
+        A = dw_dot_begin(ld(s_u, 9 * c2), nxh);
+        dw_dot_add(A, ld(s_v, 9 * c2), nyh);
         const dw V2 = dw_dot_end(A);
-        const dw mu = dw_add_fast(ld(s_a, c1), ld(s_a, c2));
+        const dw mu = dw_add_fast(ld(s_a, 9 * c1), ld(s_a, 9 * c2));
         A = dw_dot_begin(r1, V1);
         dw_dot_add(A, r2, V2);
         dw_dot_add(A, mu, r1);
@@ -199,22 +203,20 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         f[0] = dw_dot_end(A);
         A = dw_dot_begin(ru1, V1);
         dw_dot_add(A, ru2, V2);
-        dw_dot_add(A, p1, nxh);
-        dw_dot_add(A, p2, nxh);
+        dw_dot_add(A, pp, nxh);
         dw_dot_add(A, mu, ru1);
         dw_dot_add(A, mu, dw_neg(ru2));
         f[1] = dw_dot_end(A);
         A = dw_dot_begin(rv1, V1);
         dw_dot_add(A, rv2, V2);
-        dw_dot_add(A, p1, nyh);
-        dw_dot_add(A, p2, nyh);
+        dw_dot_add(A, pp, nyh);
         dw_dot_add(A, mu, rv1);
         dw_dot_add(A, mu, dw_neg(rv2));
         f[2] = dw_dot_end(A);
-        A = dw_dot_begin(ld(s_H, c1), V1);
-        dw_dot_add(A, ld(s_H, c2), V2);
-        dw_dot_add(A, mu, ld(s_E, c1));
-        dw_dot_add(A, mu, dw_neg(ld(s_E, c2)));
+        A = dw_dot_begin(ld(s_H, 9 * c1), V1);
+        dw_dot_add(A, ld(s_H, 9 * c2), V2);
+        dw_dot_add(A, mu, ld(s_E, 9 * c1));
+        dw_dot_add(A, mu, dw_neg(ld(s_E, 9 * c2)));
         f[3] = dw_dot_end(A);
     }
     if constexpr (GATHER) {
