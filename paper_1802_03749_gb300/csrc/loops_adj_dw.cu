@@ -167,7 +167,10 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         }
         s_gc[i] = (int)g;
     }
-    for (int i = tid; i < nn; i += blockDim.x) {
+    // nodes: on the warps that stage no cell when there are enough of them
+    // (two nodes per thread), so that the node loads do not follow the cell
+    // arithmetic on the cell warps
+    auto stage_node = [&](int i) {
         const int64_t g = fpn[i];
         s_x[i] = SOA ? x[g] : x[2 * g];
         s_x[cap_n + i] = SOA ? x[nnode + g] : x[2 * g + 1];
@@ -182,6 +185,16 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
             s_xi[cap_n + i] = make_float2(0.f, 0.f);
         }
         s_gn[i] = (int)g;
+    };
+    const int ncw = (nc + 31) & ~31, nfree = (int)blockDim.x - ncw;
+    if (nfree >= 32 && 2 * nfree >= nn) {
+        if (tid >= ncw) {
+            const int i = tid - ncw;
+            if (i < nn) stage_node(i);
+            if (i + nfree < nn) stage_node(i + nfree);
+        }
+    } else {
+        for (int i = tid; i < nn; i += blockDim.x) stage_node(i);
     }
     __syncthreads();
     int na = 0, nb = 0, c1 = 0, c2 = 0;

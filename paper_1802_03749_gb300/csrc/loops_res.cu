@@ -120,9 +120,12 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         if (INC == kIncColor) my_color = tcolor[d.item_start + tid];
     }
 
-    // stage cells: q, adt, per-cell primitives and the current res
-    for (int i = tid; i < nc; i += blockDim.x) {
-        int g = fpc[i];
+    // Staging: the cells (q, adt, per-cell primitives, the current res,
+    // global id, gather row) and the nodes.  When the warps that hold no
+    // cell are enough, they take the nodes (two per thread, both loads in
+    // flight together), so that node loads do not follow the cell
+    // arithmetic on the cell warps.
+    auto stage_prims = [&](int i, int g) {
         T r, ru, rv, E;
         if (SOA) {
             r = q[g];
@@ -149,30 +152,33 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         s_q[cap_c + i] = ru;
         s_q[2 * cap_c + i] = rv;
         s_q[3 * cap_c + i] = E;
-        s_adt[i] = adt[g];
         s_u[i] = u;
         s_v[i] = v;
         s_p[i] = p;
         s_H[i] = H;
-        // res is prefetched here: increments accumulate onto it in shared
-        // memory and the write-back is a plain store (blocks of one colour
-        // share no cell, so no other block touches these values meanwhile);
-        // the previous colour's launch writes it
-        mp_pdl_wait();
+    };
+    auto stage_aux = [&](int i, int g) {  // before the dependent-launch wait
+        s_adt[i] = adt[g];
+        s_gid[i] = g;
+        if (INC == kIncGather) {
+            const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
+            for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];
+        }
+    };
+    // res is prefetched: increments accumulate onto it in shared memory and
+    // the write-back is a plain store (blocks of one colour share no cell,
+    // so no other block touches these values meanwhile); the previous
+    // colour's launch writes it, so this follows the dependent-launch wait
+    auto stage_res = [&](int i, int g) {
         T r0, r1, r2, r3;
         load_res<T, SOA>(res, ncell, g, r0, r1, r2, r3);
         s_inc[i] = r0;
         s_inc[cap_c + i] = r1;
         s_inc[2 * cap_c + i] = r2;
         s_inc[3 * cap_c + i] = r3;
-        s_gid[i] = g;
-        if (INC == kIncGather) {
-            const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
-            for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];
-        }
-    }
-    // stage nodes as half coordinates (exact scaling by 1/2)
-    for (int i = tid; i < nn; i += blockDim.x) {
+    };
+    // nodes as half coordinates (exact scaling by 1/2)
+    auto stage_node = [&](int i) {
         int g = fpn[i];
         T px, py;
         if (SOA) {
@@ -189,6 +195,24 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         }
         s_xh[i] = T(0.5) * px;
         s_xh[cap_n + i] = T(0.5) * py;
+    };
+    const int ncw = (nc + 31) & ~31, nfree = (int)blockDim.x - ncw;
+    const bool split = nfree >= 32 && 2 * nfree >= nn;
+    for (int i = tid; i < nc; i += blockDim.x) {
+        const int g = fpc[i];
+        stage_prims(i, g);
+        stage_aux(i, g);
+        mp_pdl_wait();
+        stage_res(i, g);
+    }
+    if (split) {
+        if (tid >= ncw) {
+            const int i = tid - ncw;
+            if (i < nn) stage_node(i);
+            if (i + nfree < nn) stage_node(i + nfree);
+        }
+    } else {
+        for (int i = tid; i < nn; i += blockDim.x) stage_node(i);
     }
     __syncthreads();
 

@@ -157,7 +157,10 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         }
         s_gid[i] = (int)g;
     }
-    for (int i = tid; i < nn; i += blockDim.x) {
+    // nodes: on the warps that stage no cell when there are enough of them
+    // (two nodes per thread, both loads in flight together), so that the
+    // node loads do not follow the cell arithmetic on the cell warps
+    auto stage_node = [&](int i) {
         const int64_t g = fpn[i];
         if (SOA) {
             s_x[i] = x[g];
@@ -167,6 +170,16 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
             s_x[i] = a.x;
             s_y[i] = a.y;
         }
+    };
+    const int ncw = (nc + 31) & ~31, nfree = (int)blockDim.x - ncw;
+    if (nfree >= 32 && 2 * nfree >= nn) {
+        if (tid >= ncw) {
+            const int i = tid - ncw;
+            if (i < nn) stage_node(i);
+            if (i + nfree < nn) stage_node(i + nfree);
+        }
+    } else {
+        for (int i = tid; i < nn; i += blockDim.x) stage_node(i);
     }
     __syncthreads();
 
