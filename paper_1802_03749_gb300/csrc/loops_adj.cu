@@ -122,7 +122,10 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
         s_ri[i] = ri;
         s_gc[i] = (int)g;
     }
-    for (int i = tid; i < nn; i += blockDim.x) {
+    // nodes: on the warps that stage no cell when there are enough of them
+    // (two nodes per thread), so that the node loads do not follow the cell
+    // arithmetic on the cell warps
+    auto stage_node = [&](int i) {
         int64_t g = fpn[i];
         s_x[i] = SOA ? x[g] : x[2 * g];
         s_x[cap_n + i] = SOA ? x[nnode + g] : x[2 * g + 1];
@@ -130,6 +133,16 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
         s_xi[i] = SOA ? xbar[g] : xbar[2 * g];
         s_xi[cap_n + i] = SOA ? xbar[nnode + g] : xbar[2 * g + 1];
         s_gn[i] = (int)g;
+    };
+    const int ncw = (nc + 31) & ~31, nfree = (int)blockDim.x - ncw;
+    if (nfree >= 32 && 2 * nfree >= nn) {
+        if (tid >= ncw) {
+            const int i = tid - ncw;
+            if (i < nn) stage_node(i);
+            if (i + nfree < nn) stage_node(i + nfree);
+        }
+    } else {
+        for (int i = tid; i < nn; i += blockDim.x) stage_node(i);
     }
     __syncthreads();
     int na = 0, nb = 0, c1 = 0, c2 = 0;
