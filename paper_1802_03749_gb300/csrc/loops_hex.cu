@@ -152,23 +152,37 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
     }
     // stage x, v and the current f (increments accumulate onto it; blocks of
     // one colour share no node, so the write-back is a plain store)
-    for (int i = tid; i < nn; i += blockDim.x) {
-        int g = fpn[i];
-        T a, b, c;
-        load3<T, SOA>(x, nnode, g, a, b, c);
-        s_x[i] = a;
-        s_x[cap + i] = b;
-        s_x[2 * cap + i] = c;
-        load3<T, SOA>(v, nnode, g, a, b, c);
-        s_v[i] = a;
-        s_v[cap + i] = b;
-        s_v[2 * cap + i] = c;
+    // nodes, two per thread and pass: both nodes' index and data loads are
+    // issued before either is stored, so a footprint of one to two nodes per
+    // thread costs one chain of dependent loads instead of two
+    auto stage3 = [&](T *dst, int i, T a, T b, T c) {
+        dst[i] = a;
+        dst[cap + i] = b;
+        dst[2 * cap + i] = c;
+    };
+    for (int i0 = tid; i0 < nn; i0 += 2 * (int)blockDim.x) {
+        const int i1 = i0 + (int)blockDim.x;
+        const bool two = i1 < nn;
+        const int g0 = fpn[i0], g1 = two ? fpn[i1] : g0;
+        T x0[3], x1[3], v0[3], v1[3];
+        load3<T, SOA>(x, nnode, g0, x0[0], x0[1], x0[2]);
+        load3<T, SOA>(v, nnode, g0, v0[0], v0[1], v0[2]);
+        load3<T, SOA>(x, nnode, g1, x1[0], x1[1], x1[2]);
+        load3<T, SOA>(v, nnode, g1, v1[0], v1[1], v1[2]);
+        stage3(s_x, i0, x0[0], x0[1], x0[2]);
+        stage3(s_v, i0, v0[0], v0[1], v0[2]);
+        s_gid[i0] = g0;
+        if (two) {
+            stage3(s_x, i1, x1[0], x1[1], x1[2]);
+            stage3(s_v, i1, v1[0], v1[1], v1[2]);
+            s_gid[i1] = g1;
+        }
         mp_pdl_wait();  // f: written by the previous colour's launch
-        load3<T, SOA>(f, nnode, g, a, b, c);
-        s_f[i] = a;
-        s_f[cap + i] = b;
-        s_f[2 * cap + i] = c;
-        s_gid[i] = g;
+        T f0[3], f1[3];
+        load3<T, SOA>(f, nnode, g0, f0[0], f0[1], f0[2]);
+        load3<T, SOA>(f, nnode, g1, f1[0], f1[1], f1[2]);
+        stage3(s_f, i0, f0[0], f0[1], f0[2]);
+        if (two) stage3(s_f, i1, f1[0], f1[1], f1[2]);
     }
     __syncthreads();
     T fe[8][3];

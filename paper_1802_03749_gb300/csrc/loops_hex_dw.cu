@@ -101,22 +101,49 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
         l = lmap[d.item_start + tid];
         if (!GATHER) my_color = tcolor[d.item_start + tid];
     }
-    for (int i = tid; i < nn; i += blockDim.x) {
-        const int64_t g = fpn[i];
+    // nodes, two per thread and pass: both nodes' index and coordinate loads
+    // are issued before either is converted, so a block's footprint (often
+    // between one and two nodes per thread) costs one chain of dependent
+    // loads instead of two
+    auto stage_node = [&](int i, int64_t g, const double (&xv)[6]) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const int64_t j = SOA ? a * nnode + g : 3 * g + a;
-            st2(s_x, a * cap + i, dw_from_double_int(x[j]));
-            st2(s_v, a * cap + i, dw_from_double_int(v[j]));
-            mp_pdl_wait();  // f: written by the previous colour's launch
-            s_f[a * cap + i] = f[j];
-            if (!GATHER) s_i[a * cap + i] = make_float2(0.f, 0.f);
+            st2(s_x, a * cap + i, dw_from_double_int(xv[a]));
+            st2(s_v, a * cap + i, dw_from_double_int(xv[3 + a]));
         }
         if (GATHER) {
             const ushort4 *row = gat + (int64_t)(d.fp_start[0] + i) * gw4;
             for (int h = 0; h < gw4; ++h) s_ge[h * cap + i] = row[h];
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s_i[a * cap + i] = make_float2(0.f, 0.f);
         }
         s_gid[i] = (int)g;
+    };
+    auto load_xv = [&](int64_t g, double (&xv)[6]) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t j = SOA ? a * nnode + g : 3 * g + a;
+            xv[a] = x[j];
+            xv[3 + a] = v[j];
+        }
+    };
+    auto load_f = [&](int i, int64_t g) {  // f: written by the previous colour's launch
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s_f[a * cap + i] = f[SOA ? a * nnode + g : 3 * g + a];
+    };
+    for (int i0 = tid; i0 < nn; i0 += 2 * (int)blockDim.x) {
+        const int i1 = i0 + (int)blockDim.x;
+        const bool two = i1 < nn;
+        const int64_t g0 = fpn[i0], g1 = two ? fpn[i1] : g0;
+        double xv0[6], xv1[6];
+        load_xv(g0, xv0);
+        load_xv(g1, xv1);
+        stage_node(i0, g0, xv0);
+        if (two) stage_node(i1, g1, xv1);
+        mp_pdl_wait();
+        load_f(i0, g0);
+        if (two) load_f(i1, g1);
     }
     __syncthreads();
     // Per element, with C = cof(J) and B_i = C xi_i:
