@@ -23,7 +23,8 @@ from . import _build
 
 __all__ = [
     "MeshLoopError", "Plan", "lib", "loop_res_calc", "loop_bres_calc", "loop_adt_calc", "loop_save_soln",
-    "loop_res_calc_host", "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint", "loop_space_disc", "loop_getacc", "loop_face_flux", "mesh_map_renumber", "mp_check_device_status",
+    "loop_res_calc_host", "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint",
+    "loop_space_disc", "loop_getacc", "loop_face_flux", "mesh_map_renumber", "mp_check_device_status",
     "REORDER", "COLORING", "LAYOUT", "MP_MAX_BLOCK_COLORS",
 ]
 
