@@ -38,6 +38,31 @@ double now_s()
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Stable LSD radix sort of idx by key (11-bit digits, as many passes as the
+// largest key needs): equal keys keep their order in idx.
+void radix_sort(std::vector<uint64_t> &key, std::vector<int32_t> &idx)
+{
+    const size_t n = key.size();
+    uint64_t all = 0;
+    for (uint64_t k : key) all |= k;
+    int bits = 0;
+    while (bits < 64 && (all >> bits) != 0) ++bits;
+    std::vector<uint64_t> k2(n);
+    std::vector<int32_t> i2(n);
+    for (int shift = 0; shift < bits; shift += 11) {
+        size_t cnt[2049] = {0};
+        for (uint64_t k : key) cnt[((k >> shift) & 2047) + 1]++;
+        for (int d = 0; d < 2048; ++d) cnt[d + 1] += cnt[d];
+        for (size_t j = 0; j < n; ++j) {
+            const size_t to = cnt[(key[j] >> shift) & 2047]++;
+            k2[to] = key[j];
+            i2[to] = idx[j];
+        }
+        key.swap(k2);
+        idx.swap(i2);
+    }
+}
+
 // ----------------------------------------------------------------- CSR utils
 
 struct csr {
@@ -261,13 +286,22 @@ void reorder_rcm(mp_plan &P, int primary)
     }
     std::vector<int32_t> items(n);
     for (int64_t i = 0; i < n; ++i) items[i] = (int32_t)i;
-    std::sort(items.begin(), items.end(), [&](int32_t x, int32_t y) {
-        for (int k = 0; k < a; ++k) {
-            int32_t kx = keys[(int64_t)x * a + k], ky = keys[(int64_t)y * a + k];
-            if (kx != ky) return kx < ky;
-        }
-        return x < y;
-    });
+    if (a <= 2) {
+        // the (at most two) non-negative 31-bit keys packed in one word:
+        // a stable radix sort from ascending ids gives the same order
+        std::vector<uint64_t> packed(n);
+        for (int64_t i = 0; i < n; ++i)
+            packed[i] = a == 1 ? (uint64_t)keys[i] : ((uint64_t)keys[2 * i] << 31) | (uint64_t)keys[2 * i + 1];
+        radix_sort(packed, items);
+    } else {
+        std::sort(items.begin(), items.end(), [&](int32_t x, int32_t y) {
+            for (int k = 0; k < a; ++k) {
+                int32_t kx = keys[(int64_t)x * a + k], ky = keys[(int64_t)y * a + k];
+                if (kx != ky) return kx < ky;
+            }
+            return x < y;
+        });
+    }
     permute_items(P, items);
     // other to-sets: first touch over the sorted iterations, map then slot order
     for (int s = 0; s < P.ntosets; ++s) {
@@ -720,15 +754,34 @@ std::vector<int32_t> data_point_order(const mp_plan &P, int slot)
                     }
                 }
             }
-    std::vector<int32_t> order(np);
-    for (int64_t p = 0; p < np; ++p) order[p] = (int32_t)p;
-    std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        int32_t cx = cnt[x] ? cnt[x] : INT32_MAX, cy = cnt[y] ? cnt[y] : INT32_MAX;
-        if (cx != cy) return cx < cy;
+    // Points of one or two blocks (most of them) are ordered by a packed key
+    // (count, first block, second block) with a stable radix sort from
+    // ascending ids; points of three or more blocks follow, compared list by
+    // list; points of no block go last, by id.
+    std::vector<uint64_t> key;
+    std::vector<int32_t> order, many, none;
+    key.reserve(np);
+    order.reserve(np);
+    for (int64_t p = 0; p < np; ++p) {
+        if (cnt[p] == 1 || cnt[p] == 2) {
+            const uint64_t b0 = (uint64_t)lst[off[p]], b1 = cnt[p] == 2 ? (uint64_t)lst[off[p] + 1] : 0;
+            key.push_back(((uint64_t)cnt[p] << 62) | (b0 << 31) | b1);
+            order.push_back((int32_t)p);
+        } else if (cnt[p] > 2) {
+            many.push_back((int32_t)p);
+        } else {
+            none.push_back((int32_t)p);
+        }
+    }
+    radix_sort(key, order);
+    std::sort(many.begin(), many.end(), [&](int32_t x, int32_t y) {
+        if (cnt[x] != cnt[y]) return cnt[x] < cnt[y];
         for (int32_t k = 0; k < cnt[x]; ++k)
             if (lst[off[x] + k] != lst[off[y] + k]) return lst[off[x] + k] < lst[off[y] + k];
         return x < y;
     });
+    order.insert(order.end(), many.begin(), many.end());
+    order.insert(order.end(), none.begin(), none.end());
     return order;
 }
 
