@@ -153,6 +153,28 @@ def test_partition_data_reorder_groups_points(mesh):
     assert order == list(range(m.ncell))
 
 
+@pytest.mark.parametrize("reorder", ["rcm", "partition"])
+def test_data_point_order_all_key_groups(reorder):
+    """Data-point order of both to-sets on a random map with points of one,
+    two, three or more blocks and points no iteration touches (unused ids
+    at the top of each set), against the oracle's key."""
+    rng = np.random.default_rng(7)
+    n, nn, nc = 3000, 900, 700
+    e2n = rng.integers(0, nn - 60, size=(n, 2), dtype=np.int32)
+    e2c = rng.integers(0, nc - 40, size=(n, 3), dtype=np.int32)
+    maps = [{"to_set": 1, "idx": e2n, "to_size": nn, "written": False},
+            {"to_set": 2, "idx": e2c, "to_size": nc, "written": True}]
+    P = ml.Plan(maps, n, block_size=64, reorder=reorder, coloring="hier", data_reorder=1)
+    bo = P.table("block_offsets")
+    blk = np.repeat(np.arange(len(bo) - 1), np.diff(bo))
+    pn = P.table("map", 0).reshape(-1, 2)
+    pc = P.table("map", 1).reshape(-1, 3)
+    counts = [len({int(b) for b in blk[np.any(pc == p, axis=1)]}) for p in range(nc)]
+    assert max(counts) >= 3 and min(counts) == 0
+    assert PO.data_point_order(blk, [pn], nn) == list(range(nn))
+    assert PO.data_point_order(blk, [pc], nc) == list(range(nc))
+
+
 def test_errors():
     idx = np.array([[0, 1], [1, 5]], dtype=np.int32)
     with pytest.raises(ml.MeshLoopError) as e:
