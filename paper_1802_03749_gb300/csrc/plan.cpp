@@ -552,10 +552,14 @@ void split_last_color(const mp_plan &P, std::vector<int32_t> &color, int32_t &nc
 //     inside it frees c for B (the swap keeps the colouring valid).
 // Stops at the first colour that cannot be emptied completely (the blocks
 // already moved stay moved: still a valid colouring).  Deterministic.
+// Plans with more than 64 colours (blocks of an unordered mesh) keep their
+// first-fit colours: one launch in that many matters little, and the colour
+// pairs the interchanges try (quadratic in the colours, each over the
+// block's neighbours) would dominate the build.
 void reduce_sparse_colors(const mp_plan &P, std::vector<int32_t> &color, int32_t &ncolors)
 {
     const int32_t nb = P.nblocks;
-    if (nb < 2 || ncolors < 2) return;
+    if (nb < 2 || ncolors < 2 || ncolors > 64) return;
     // block adjacency through shared written points
     std::vector<int32_t> off[MP_MAX_TOSETS], lst[MP_MAX_TOSETS];
     std::vector<std::pair<int, int32_t>> pts;
