@@ -175,6 +175,25 @@ def test_data_point_order_all_key_groups(reorder):
     assert PO.data_point_order(blk, [pc], nc) == list(range(nc))
 
 
+def test_many_block_colours_keep_first_fit():
+    """Above 64 block colours the default plan keeps the first-fit block
+    colouring (no trailing-colour removal): same colours as recolor=0."""
+    rng = np.random.default_rng(11)
+    n, nc = 20000, 5000  # about 100 block colours
+    e2c = rng.integers(0, nc, size=(n, 2), dtype=np.int32)
+    maps = [{"to_set": 1, "idx": e2c, "to_size": nc, "written": True}]
+    P = ml.Plan(maps, n, block_size=32, reorder="none", coloring="hier")
+    Q = ml.Plan(maps, n, block_size=32, reorder="none", coloring="hier", recolor=0)
+    assert P.stats()["nblock_colors"] > 64
+    for t in ("block_offsets", "block_color", "thread_color"):
+        assert np.array_equal(P.table(t), Q.table(t))
+    bo = P.table("block_offsets")
+    wrows = PO.written_rows_of([{"to_set": 1, "idx": P.table("map", 0).reshape(-1, 2), "to_size": nc,
+                                 "written": True}])
+    blocks = [list(range(bo[b], bo[b + 1])) for b in range(len(bo) - 1)]
+    assert list(P.table("block_color")) == PO.block_colors(blocks, wrows)
+
+
 def test_errors():
     idx = np.array([[0, 1], [1, 5]], dtype=np.int32)
     with pytest.raises(ml.MeshLoopError) as e:
