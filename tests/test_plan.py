@@ -124,6 +124,25 @@ def test_rcm_matches_oracle(mesh):
     assert np.array_equal(P.perm(1), ref[1])
 
 
+@pytest.mark.parametrize("case", ["bedge_arity1", "cell2node_arity4"])
+def test_rcm_matches_oracle_other_arities(mesh, case):
+    """The RCM reorder with a primary map of arity 1 (boundary edge -> cell)
+    and of arity 4 (cell -> node): iteration order by the sorted tuple of
+    renumbered primary points, ties by old id."""
+    m = mesh
+    if case == "bedge_arity1":
+        maps = [{"to_set": 1, "idx": m.bedge2node, "to_size": m.nnode, "written": False},
+                {"to_set": 2, "idx": m.bedge2cell.reshape(-1, 1), "to_size": m.ncell, "written": True}]
+        n, primary, sets = m.bedge2cell.shape[0], 1, (0, 1, 2)
+    else:
+        maps = [{"to_set": 1, "idx": m.cell2node, "to_size": m.nnode, "written": True}]
+        n, primary, sets = m.ncell, 0, (0, 1)
+    P = ml.Plan(maps, n, block_size=64, reorder="rcm", coloring="atomic")
+    ref = PO.rcm_plan_perms(maps, n, primary=primary)
+    for s in sets:
+        assert np.array_equal(P.perm(s), ref[s])
+
+
 def test_global_coloring_matches_oracle(mesh):
     m = mesh
     P = ml.Plan(res_maps(m), m.nedge, block_size=256, reorder="rcm", coloring="global")
