@@ -116,13 +116,17 @@ typedef struct {
                             default (hex assembly, whose 3D blocks need ~10 thread
                             colours: MP_STAGED_SMEM_ATOMIC in FP32, MP_STAGED_WARP_AGG
                             in FP64; MP_STAGED_GATHER for FP32
-                            and double-word res_calc and the increment-only loops;
+                            and double-word res_calc, the double-word hex assembly
+                            and adjoint, and the increment-only loops;
                             MP_STAGED_SIMPLE otherwise)                               */
     int32_t recolor;     /* HIER: after the first-fit block colouring, empty the last
                             colours when they hold few blocks (at most 1/32 of them)
                             by moving each of their blocks to an earlier colour
                             whose conflicting blocks (at most two) can themselves
-                            move to a third colour: fewer, fuller launches.
+                            move to a third colour, by a two-colour interchange,
+                            or split into pieces that fit earlier colours: fewer,
+                            fuller launches.  Plans with more than 64 block
+                            colours keep first fit.
                             0: off (the first-fit colouring alone), 1: on,
                             -1: default (on)                                         */
     const int32_t *block_of; /* optional, host, from_size entries: caller-defined
