@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(1024) adjoint_hier(const mp_block_desc *__rest
         s_gc[i] = (int)g;
     }
     // nodes: on the warps that stage no cell when there are enough of them
-    // (two nodes per thread), so that the node loads do not follow the cell
+    // (at most two nodes per thread), so that the node loads do not follow the cell
     // arithmetic on the cell warps
     auto stage_node = [&](int i) {
         int64_t g = fpn[i];

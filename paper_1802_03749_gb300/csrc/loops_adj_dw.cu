@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         s_gc[i] = (int)g;
     }
     // nodes: on the warps that stage no cell when there are enough of them
-    // (two nodes per thread), so that the node loads do not follow the cell
+    // (at most two nodes per thread), so that the node loads do not follow the cell
     // arithmetic on the cell warps
     auto stage_node = [&](int i) {
         const int64_t g = fpn[i];

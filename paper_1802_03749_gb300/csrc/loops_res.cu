@@ -122,9 +122,8 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
 
     // Staging: the cells (q, adt, per-cell primitives, the current res,
     // global id, gather row) and the nodes.  When the warps that hold no
-    // cell are enough, they take the nodes (two per thread, both loads in
-    // flight together), so that node loads do not follow the cell
-    // arithmetic on the cell warps.
+    // cell are enough, they take the nodes (at most two per thread), so
+    // that node loads do not follow the cell arithmetic on the cell warps.
     auto stage_prims = [&](int i, int g) {
         T r, ru, rv, E;
         if (SOA) {

@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         s_gid[i] = (int)g;
     }
     // nodes: on the warps that stage no cell when there are enough of them
-    // (two nodes per thread, both loads in flight together), so that the
-    // node loads do not follow the cell arithmetic on the cell warps
+    // (at most two nodes per thread), so that the node loads do not follow
+    // the cell arithmetic on the cell warps
     auto stage_node = [&](int i) {
         const int64_t g = fpn[i];
         if (SOA) {
