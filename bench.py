@@ -2,13 +2,22 @@
 other loops of the library, on synthetic meshes shaped like the paper's.
 
 Headline workload: res_calc on a jittered, randomly renumbered 2400x1200 quad
-mesh (2,880,000 cells, 5,756,400 interior edges) with FP64 data, through the
-C ABI.  A step is one full res_calc pass (every block colour) of the
-two-layer staged kernel (RCM + partition plan).  The metric is interior
-edges per second; useful bandwidth follows the paper's formula (Sec. 3.1:
-each dataset once, twice if read and written, maps as int32 datasets).
+mesh (2,880,000 cells, 5,756,400 interior edges) with FP64 data and native
+FP64 arithmetic (the paper's precision, Table 2), through the C ABI.  A step
+is one full res_calc pass (every block colour) of the two-layer staged
+kernel on an RCM + partition plan.  The metric is interior edges per second;
+useful bandwidth follows the paper's formula (Sec. 3.1: each dataset once,
+twice if read and written, maps as int32 datasets).
+
+Timing protocol: after max(W, 10) warm-up calls, 5 repetitions of n calls
+(n >= max(K, 100) and long enough for 0.1 s per repetition), each bracketed
+by a barrier and a device synchronisation and timed by CUDA events on the
+launching stream; the median repetition gives ms per call.  Two regimes:
+warm (calls back to back; the inputs exceed L2) and L2-flushed (a write of
+twice the L2 size before every call, each call timed by its own events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--compute f64|dw|f32]
 
 Prints one JSON line on rank 0.  Under torchrun every rank runs an
 independent replica of the workload (no collective on the data path); the
@@ -17,7 +26,9 @@ value is the edges of all ranks over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -35,6 +46,11 @@ METRIC = "res_calc Gedges/s & HBM GB/s % of peak: two-layer vs atomics vs global
 NX, NY = 2400, 1200
 GAM, EPS = 1.4, 0.05
 L2_BYTES = 129 * 10 ** 6
+REPS = 5
+MIN_CALLS = 100
+MIN_WARMUP = 10
+MIN_REP_SECONDS = 0.1
+FIELDS = ("rho", "rho_u", "rho_v", "E")
 
 # algorithmic floating-point operations of one interior edge as the oracle
 # evaluates it: two normal fluxes of 20 (pressure 7, normal velocity 4,
@@ -43,37 +59,93 @@ L2_BYTES = 129 * 10 ** 6
 FLOPS_PER_EDGE = 73
 # FP64 FMA throughput of GB300: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Double-word arithmetic: the res_calc flux uses 26 additions of 11 FP32
-# operations and 19 products of 8, 9.7 FP32 operations per double-word
-# operation, on 152 SMs x 128 FP32 lanes x 2.07 GHz
-DW_FP32_OPS_PER_OP = 9.7
-DW_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DW_FP32_OPS_PER_OP / 1e12
+# FP32 FMA throughput: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM traffic records: one text file per configuration under profiles/,
+# written by --record-traffic from an ncu CSV of the headline kernel
+TRAFFIC_SOURCES = ("loops_res.cu", "loops_res_dw.cu", "dw.cuh", "common.cuh", "plan_internal.h", "plan.cpp")
+HEAD_KERNEL = {"f64": "res_calc_hier", "f32": "res_calc_hier", "dw": "res_calc_hier_dw"}
 
 
-# DRAM bytes (read + write) of one pass of the headline kernel (all block
-# colours: double-word res_calc, gather increments, 2400x1200, block 256,
-# partitioned) from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum over the 4 launches of a pass; summary in
-# profiles/res_calc_hier_dw_2400x1200.md).  Valid only for the sources it
-# was measured on: a change to any of them reports null until re-measured.
-HEADLINE_TRAFFIC = {"bytes_per_pass": 416253952, "launches_per_pass": 4,
-                    "config": ("dw", "gather", 256, 2400, 1200, "aos"),
-                    "sha256": "ffa4749a30bc752f8ae7c794d691a0db127651c7afeace5f3f687deff2564325",
-                    "sources": ("loops_res_dw.cu", "dw.cuh", "plan.cpp")}
-
-
-def headline_traffic(args, head_staged):
-    """Measured DRAM bytes per pass when the kernel sources and the launch
-    configuration are the ones the capture was taken on, else None."""
-    import hashlib
-    T = HEADLINE_TRAFFIC
-    if (args.compute, head_staged, args.block_size, args.nx, args.ny, args.layout) != T["config"]:
-        return None
+def sources_sha256():
+    """Hash of the sources the headline kernels and their plans compile from."""
     h = hashlib.sha256()
-    for f in T["sources"]:
+    for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_1802_03749_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return T["bytes_per_pass"] if h.hexdigest() == T["sha256"] else None
+    return h.hexdigest()
+
+
+def traffic_path(compute, nx, ny):
+    return os.path.join(ROOT, "profiles", f"traffic_res_calc_{compute}_{nx}x{ny}.txt")
+
+
+def read_traffic(compute, staged, args):
+    """The recorded DRAM bytes of one headline pass when the record's
+    configuration and source hash match the running one, else None (with
+    the reason)."""
+    p = traffic_path(compute, args.nx, args.ny)
+    if not os.path.exists(p):
+        return None, "no capture recorded for this configuration"
+    rec = {}
+    with open(p) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                rec[k.strip()] = v.strip()
+    want = {"compute": compute, "staged": staged, "block": str(args.block_size), "layout": args.layout}
+    if any(rec.get(k) != v for k, v in want.items()):
+        return None, "recorded for another launch configuration"
+    if rec.get("sources_sha256") != sources_sha256():
+        return None, "kernel or planner sources changed since the capture"
+    return {k: (int(v) if v.isdigit() else v) for k, v in rec.items()}, "ncu capture of the current sources"
+
+
+def record_traffic(args):
+    """Write profiles/traffic_res_calc_<compute>_<nx>x<ny>.txt from an ncu CSV
+    (``--csv --print-units base --metrics dram__bytes_read.sum,
+    dram__bytes_write.sum,gpu__time_duration.sum``) of consecutive headline
+    passes: DRAM bytes per pass = bytes over the captured launches x the
+    launches of one pass / captured launches."""
+    import csv
+    rows = {}
+    with open(args.record_traffic) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        if HEAD_KERNEL[args.compute] + "<" not in r.get("Kernel Name", "") and \
+                HEAD_KERNEL[args.compute] + "(" not in r.get("Kernel Name", ""):
+            continue
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1, "usecond": 1e3,
+                 "msecond": 1e6}.get(r["Metric Unit"], 1)
+        rows.setdefault(r["ID"], {})[r["Metric Name"]] = float(r["Metric Value"].replace(",", "")) * scale
+    if not rows:
+        raise SystemExit(f"no {HEAD_KERNEL[args.compute]} launches in {args.record_traffic}")
+    n = len(rows)
+    lpp = args.launches_per_pass
+    rd = sum(v.get("dram__bytes_read.sum", 0) for v in rows.values())
+    wr = sum(v.get("dram__bytes_write.sum", 0) for v in rows.values())
+    ns = sum(v.get("gpu__time_duration.sum", 0) for v in rows.values())
+    staged = args.staged or default_staged(args.compute)
+    out = traffic_path(args.compute, args.nx, args.ny)
+    with open(out, "w") as f:
+        f.write(f"# DRAM traffic of one res_calc pass ({lpp} block-colour launches of {HEAD_KERNEL[args.compute]}),\n"
+                f"# {args.nx}x{args.ny} quads, from {n} consecutive launches captured with ncu --cache-control none\n"
+                f"# (dirty lines of one launch are written back during the following ones, so writes are counted).\n"
+                f"# command: {args.record_command}\n")
+        for k, v in (("compute", args.compute), ("staged", staged), ("block", args.block_size),
+                     ("layout", args.layout), ("nx", args.nx), ("ny", args.ny), ("launches_captured", n),
+                     ("launches_per_pass", lpp), ("read_bytes_per_pass", int(round(rd * lpp / n))),
+                     ("write_bytes_per_pass", int(round(wr * lpp / n))),
+                     ("bytes_per_pass", int(round((rd + wr) * lpp / n))),
+                     ("ncu_ns_per_pass", int(round(ns * lpp / n))), ("sources_sha256", sources_sha256())):
+            f.write(f"{k}={v}\n")
+    print(open(out).read())
+
+
+def default_staged(compute):
+    """The library's default increment form of the headline kernel."""
+    return "simple" if compute == "f64" else "gather"
 
 
 def useful_bytes_res_calc(ncell, nnode, nedge, elt):
@@ -107,6 +179,16 @@ def synthetic_adt(m):
     """A positive per-cell time-step field of the magnitude the free stream
     gives on an h x h cell ((2h(|u|+|v|) + 4h)/0.9, about 5.4 h)."""
     return meshgen.positive_field(m.ncell, 5.0 * m.h, 6.0 * m.h)
+
+
+def rel_l2(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / (nb if nb > 0 else 1.0))
+
+
+def field_errors(got, ref):
+    """rel-L2 over all components and per field (rho, rho u, rho v, E)."""
+    return {"rel_l2": rel_l2(got, ref), "per_field": {f: rel_l2(got[:, k], ref[:, k]) for k, f in enumerate(FIELDS)}}
 
 
 class ClockSampler:
@@ -143,10 +225,11 @@ class ClockSampler:
                 continue
             try:
                 sm, smax = float(f[0]), float(f[1])
+                pw = float(f[2])
             except ValueError:
                 continue
             reasons = [n for n, v in zip(self.NAMES, f[3:7]) if v.lower().startswith("active")]
-            self.samples.append((time.time(), sm, smax, reasons))
+            self.samples.append((time.time(), sm, smax, reasons, pw))
 
     def stop(self):
         if self.proc is not None:
@@ -165,7 +248,9 @@ class ClockSampler:
         if not s:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         return {"sm_mhz": float(np.median([x[1] for x in s])), "sm_max_mhz": max(x[2] for x in s),
-                "reasons": sorted({r for x in s for r in x[3]}), "samples": len(s), "window": kind}
+                "sm_mhz_min": min(x[1] for x in s), "power_w_max": max(x[4] for x in s),
+                "reasons": sorted({r for x in s for r in x[3]}), "samples": len(s), "window": kind,
+                "seconds": round(t1 - t0, 3)}
 
 
 def dist_setup():
@@ -173,15 +258,15 @@ def dist_setup():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def max_over_ranks(ms, dist, device="cpu"):
-    """Slowest rank's time (replicas run independently; the job ends with
-    the slowest).  ``dist`` is torch.distributed or None for one process."""
+def max_over_ranks(vals, dist, device="cpu"):
+    """Element-wise slowest rank's times (replicas run independently; the
+    job ends with the slowest).  ``dist`` is torch.distributed or None."""
     if dist is None:
-        return ms
+        return list(vals)
     import torch
-    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    t = torch.tensor(list(vals), dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return [float(v) for v in t.tolist()]
 
 
 def job_rate(units_per_rank, world, ms_per_step):
@@ -189,19 +274,151 @@ def job_rate(units_per_rank, world, ms_per_step):
     return world * units_per_rank / (ms_per_step * 1e-3)
 
 
-def oracle_res_calc_rate(m, q, adt, budget_s):
-    """The oracle's sequential res_calc on the host, repeated for ~budget_s."""
+class Protocol:
+    """CUDA-event timing on the current stream after the measurement
+    protocol: warm-up calls, then repetitions of n calls, each bracketed by
+    a barrier and a device synchronisation; the median repetition (max over
+    ranks) gives ms per call.  ``flushed`` writes a buffer of twice the L2
+    size before every call and times each call by its own event pair."""
+
+    def __init__(self, torch, dist):
+        self.torch, self.dist = torch, dist
+        self.flush_buf = None
+
+    def _fence(self):
+        torch = self.torch
+        torch.cuda.synchronize()
+        if self.dist is not None:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+
+    def calls_for(self, fn, min_calls, warmup):
+        """Warm up, then the calls per repetition: at least ``min_calls`` and
+        enough for MIN_REP_SECONDS at the estimated rate."""
+        torch = self.torch
+        for _ in range(warmup):
+            fn()
+        self._fence()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s = torch.cuda.current_stream()
+        e0.record(s)
+        for _ in range(10):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        est = max(e0.elapsed_time(e1) / 10, 1e-4)
+        n = max(min_calls, int(math.ceil(MIN_REP_SECONDS * 1e3 / est)))
+        return int(max_over_ranks([n], self.dist, "cuda")[0])
+
+    def warm(self, fn, calls, reps):
+        torch = self.torch
+        s = torch.cuda.current_stream()
+        times = []
+        t0 = time.time()
+        for _ in range(reps):
+            self._fence()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(calls):
+                fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / calls)
+        t1 = time.time()
+        times = max_over_ranks(times, self.dist, "cuda")
+        return float(np.median(times)), times, (t0, t1)
+
+    def flushed(self, fn, calls, reps):
+        torch = self.torch
+        if self.flush_buf is None:
+            self.flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+        s = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+        times = []
+        t0 = time.time()
+        for r in range(reps):
+            self._fence()
+            for i in range(calls):
+                self.flush_buf.fill_(r * calls + i)
+                ev[i][0].record(s)
+                fn()
+                ev[i][1].record(s)
+            torch.cuda.synchronize()
+            times.append(sum(a.elapsed_time(b) for a, b in ev) / calls)
+        t1 = time.time()
+        times = max_over_ranks(times, self.dist, "cuda")
+        return float(np.median(times)), times, (t0, t1)
+
+    def __call__(self, fn, calls, warmup, reps=3):
+        """Warm regime with ``calls`` calls per repetition (the other loops'
+        rows): median ms per call and the host time window."""
+        for _ in range(warmup):
+            fn()
+        ms, _, win = self.warm(fn, calls, reps)
+        return ms, win
+
+
+def oracle_leg(m, q, adt, budget_s):
+    """CPU baseline: the oracle's sequential FP64 res_calc on the host,
+    repeated for about ``budget_s`` seconds.  Its result is kept: it is the
+    expected value of the error figures reported beside each GPU variant."""
     import oracle
     res = np.zeros((m.ncell, 4))
     n = 0
     t0 = time.perf_counter()
     while True:
+        res[:] = 0.0
         oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt, res=res)
         n += 1
         dt = time.perf_counter() - t0
         if dt >= budget_s:
             break
-    return n * m.nedge / dt / 1e9, n, dt
+    return n * m.nedge / dt / 1e9, n, dt, res
+
+
+def oracle_res_f32_inputs(m, q, adt):
+    """The oracle's FP64 res_calc on the FP32-rounded inputs: what the FP32
+    path computes, up to its own arithmetic."""
+    import oracle
+    r = lambda a: np.asarray(a).astype(np.float32).astype(np.float64)
+    return oracle.res_calc(m.edge2node, m.edge2cell, r(m.x), r(q), r(adt))
+
+
+def precision_rows(ml, torch, steps=(1, 2, 5, 10, 20, 50, 100)):
+    """FP32 storage with the FP64 update and residual sum, against the FP64
+    oracle, per field and per step count: the 200x100 Airfoil-style time
+    step (save_soln, adt_calc, res_calc, bres_calc, update).  Reported: q's
+    rel-L2 per field (against the oracle started from the FP32-rounded state
+    and from the exact state), the rel-L2 of the accumulated change
+    q_k - q_0, and the relative error of the RMS residual."""
+    import oracle
+    from paper_1802_03749_gb300.mesh import AirfoilPlans, AirfoilStep
+    m = meshgen.quad_mesh(200, 100)
+    q0 = meshgen.quad_state(m.ncell)
+    qinf = meshgen.freestream()
+    P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
+                     block_size=256, reorder="partition", coloring="hier")
+    S = AirfoilStep(P, m.x, q0, qinf, dtype="f32")
+    q_s = q0.astype(np.float32).astype(np.float64)   # the stored initial state
+    q_r = q_s.copy()                                  # the oracle from the stored initial state
+    q_e = q0.copy()                                   # the oracle from the exact state
+    out = {}
+    for k in range(1, max(steps) + 1):
+        S.rms.zero_()
+        S.step()
+        torch.cuda.synchronize()
+        rms_ref, _ = oracle.step(m, q_r, qinf)
+        oracle.step(m, q_e, qinf)
+        if k in steps:
+            got = S.q_original()
+            rms = float(np.sqrt(S.rms.item() / m.ncell))
+            out[str(k)] = {
+                "q_per_field": {f: rel_l2(got[:, i], q_r[:, i]) for i, f in enumerate(FIELDS)},
+                "q_per_field_vs_exact_start": {f: rel_l2(got[:, i], q_e[:, i]) for i, f in enumerate(FIELDS)},
+                "dq_per_field": {f: rel_l2(got[:, i] - q_s[:, i], q_r[:, i] - q_s[:, i]) for i, f in enumerate(FIELDS)},
+                "rms_rel_err": abs(rms - rms_ref) / rms_ref}
+    return {"workload": "Airfoil-style time step 200x100, FP32 storage and arithmetic, FP64 update and residual sum, "
+                        "against the FP64 oracle", "steps": out}
 
 
 def run_reference(args):
@@ -233,37 +450,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-class Timer:
-    """CUDA-event timing of a callable on the current stream, with a
-    barrier and synchronisation on both sides and max over ranks."""
-
-    def __init__(self, torch, dist):
-        self.torch, self.dist = torch, dist
-
-    def __call__(self, fn, steps, warmup):
-        torch, dist = self.torch, self.dist
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        stream = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0 = time.time()
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t1 = time.time()
-        ms = max_over_ranks(e0.elapsed_time(e1), dist, device="cuda")
-        return ms / steps, (t0, t1)
-
-
 def bench_rows(ml, torch, timer, args):
-    """Measurements of the other loops (not the headline): hex assembly,
-    the adjoint and the batched graph-captured time step (``--rows``)."""
+    """Measurements of the other loops (not the headline, ``--rows``): hex
+    assembly, the adjoint, the batched graph-captured time step, handcrafted
+    block shapes, the increment-only loops, the face flux and the FP32
+    error per field and step count.  ``timer(fn, calls, warmup)`` is the
+    warm regime of the protocol with 3 repetitions."""
     rows = {}
     want = set(args.rows.split(",")) if args.rows and args.rows != "none" else set()
     if "hex" in want:
@@ -278,6 +470,8 @@ def bench_rows(ml, torch, timer, args):
         rows.update(bench_increment(ml, torch, timer, args))
     if "face" in want:
         rows.update(bench_face(ml, torch, timer, args))
+    if "precision" in want and dist_setup()[1] == 0:
+        rows["precision_f32_steps"] = precision_rows(ml, torch)
     return rows
 
 
@@ -335,8 +529,8 @@ def bench_face(ml, torch, timer, args):
 
 
 def bench_increment(ml, torch, timer, args):
-    """The increment-only loops at the paper's mesh sizes (Sec. 3.1.3 and
-    3.1.4): the Volna-style edge loop in FP32 on 1100x1100 quads split into
+    """The increment-only loops at the paper's mesh sizes (Sec. 3.1.2 and
+    3.1.3): the Volna-style edge loop in FP32 on 1100x1100 quads split into
     2.42M triangles (3.63M edges; the paper's mesh has 2.4M triangles and
     3.59M edges), the BookLeaf-style cell loop in FP64 on 2000x2000 quads
     (4M cells).  Useful bytes: each dataset once (twice if incremented),
@@ -415,10 +609,12 @@ def bench_hex(ml, torch, timer, args):
                 "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
                 "reuse": st["reuse_all"]}
             del x, vd, sd, f, vol
-    # hex assembly with FP64 data in double-word arithmetic (two-layer, S = 128):
-    # gather increments (default) and thread colours, partitioned and RCM
-    for reorder in ("partition", "rcm"):
-        H = HexPlan(hm.nnode, hm.elem2node, block_size=128, reorder=reorder, coloring="hier")
+    # hex assembly with FP64 data in double-word arithmetic: two-layer (S =
+    # 128; gather increments, the default, and thread colours, partitioned
+    # and RCM) and the atomics and global-colour baselines in the same
+    # arithmetic
+    for coloring, reorder in (("hier", "partition"), ("hier", "rcm"), ("atomic", "rcm"), ("global", "rcm")):
+        H = HexPlan(hm.nnode, hm.elem2node, block_size=128, reorder=reorder, coloring=coloring)
         H.plan.upload()
         x = torch.tensor(H.to_plan(hm.x, "node"), device="cuda")
         vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
@@ -427,10 +623,11 @@ def bench_hex(ml, torch, timer, args):
         vol = torch.zeros(hm.nelem, dtype=torch.float64, device="cuda")
         ub = useful_bytes_hex(hm.nelem, hm.nnode, 8)
         st = H.plan.stats()
-        for staged in ("gather", "simple"):
-            H.plan.set_staged(staged)
+        for staged in (("gather", "simple") if coloring == "hier" else (None,)):
+            if staged:
+                H.plan.set_staged(staged)
             ms, _ = timer(lambda: ml.loop_elem_assemble(H.plan, x, vd, sd, f, vol, 0.01, compute="dw"), 10, 2)
-            rows[f"hex_f64dw_hier_{reorder}_{staged}"] = {
+            rows[f"hex_f64dw_{coloring}_{reorder}" + (f"_{staged}" if staged else "")] = {
                 "workload": f"hex assembly {args.hex_n}^3 elements, double-word arithmetic", "ms": ms,
                 "gelems_s": hm.nelem / ms / 1e6, "useful_gbs": ub / ms / 1e6, "frac_hbm": ub / ms / 1e6 / hbm,
                 "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
@@ -516,49 +713,112 @@ def bench_batch(ml, torch, timer, args):
     B.capture(steps_per_graph=1)
     ms_graph, _ = timer(lambda: B.graph.replay(), 20, 3)
     ms_batch_eager, _ = timer(B.step, 20, 3)
+    # the same meshes with the same plans (the autotuner's choice per mesh),
+    # one step per mesh: eagerly (64 launch sequences) and as 64 graphs
     per = [AirfoilStep(AirfoilPlans(mm.ncell, mm.nnode, mm.edge2node, mm.edge2cell, mm.bedge2node, mm.bedge2cell,
-                                    mm.cell2node, block_size=480, reorder="partition"), mm.x, s, qinf, dtype="f32")
-           for mm, s in zip(meshes, states)]
+                                    mm.cell2node, block_size=c[0], reorder=c[1], coloring=c[2]), mm.x, s, qinf,
+                       dtype="f32")
+           for mm, s, c in zip(meshes, states, choices)]
 
     def per_mesh():
         for S in per:
             S.step()
 
     ms_per, _ = timer(per_mesh, 5, 1)
+    for S in per:
+        S.capture(steps_per_graph=1)
+
+    def per_mesh_graphs():
+        for S in per:
+            S.graph.replay()
+
+    ms_per_graphs, _ = timer(per_mesh_graphs, 10, 2)
     cells = sum(mm.ncell for mm in meshes)
     edges = sum(mm.nedge for mm in meshes)
     rows["batch_step_f32"] = {
         "workload": f"{args.batch} quad meshes, {cells} cells, {edges} edges, full time step, FP32 data, "
                     "FP64 update and residual sum",
         "ms_graph_batched": ms_graph, "ms_eager_batched": ms_batch_eager, "ms_per_mesh_launches": ms_per,
-        "speedup_vs_per_mesh": ms_per / ms_graph, "gedges_s": edges / ms_graph / 1e6,
+        "ms_per_mesh_graphs": ms_per_graphs, "speedup_vs_per_mesh": ms_per / ms_graph,
+        "speedup_vs_per_mesh_graphs": ms_per_graphs / ms_graph, "gedges_s": edges / ms_graph / 1e6,
         "autotune": tuned, "autotune_seconds": tune_s}
     return rows
+
+
+def res_variants(compute_head):
+    """The comparison matrix of res_calc: (plan key, name, arithmetic,
+    staged form).  Plans: (colouring, reordering, layout, first-fit colours)."""
+    part, part_ff, rcm = ("hier", "partition", "aos", False), ("hier", "partition", "aos", True), \
+        ("hier", "rcm", "aos", False)
+    g_rcm, g_none = ("global", "rcm", "aos", False), ("global", "none", "aos", False)
+    a_rcm, a_none = ("atomic", "rcm", "aos", False), ("atomic", "none", "aos", False)
+    t_rcm = ("twostep", "rcm", "aos", False)
+    part_soa, a_rcm_soa = ("hier", "partition", "soa", False), ("atomic", "rcm", "soa", False)
+    g_rcm_soa = ("global", "rcm", "soa", False)
+    v = [
+        # FP64 data, native FP64 arithmetic (the paper's precision)
+        (part, "two_layer_partition_f64_simple", "f64", "simple"),
+        (part, "two_layer_partition_f64_gather", "f64", "gather"),
+        (part, "two_layer_partition_f64_smem_atomic", "f64", "smem_atomic"),
+        (part, "two_layer_partition_f64_warp_agg", "f64", "warp_agg"),
+        (part, "two_layer_partition_f64_pipelined", "f64", "pipelined"),
+        (part_ff, "two_layer_partition_f64_first_fit_colours", "f64", "simple"),
+        (rcm, "two_layer_rcm_f64", "f64", None),
+        (g_rcm, "global_rcm_f64", "f64", None), (g_none, "global_none_f64", "f64", None),
+        (a_rcm, "atomic_rcm_f64", "f64", None), (a_none, "atomic_none_f64", "f64", None),
+        (t_rcm, "twostep_rcm_f64", "f64", None),
+        # FP64 data, double-word arithmetic on the FP32 pipes
+        (part, "two_layer_partition_dw_gather", "dw", "gather"),
+        (part, "two_layer_partition_dw_simple", "dw", "simple"),
+        (part_ff, "two_layer_partition_dw_first_fit_colours", "dw", "gather"),
+        (rcm, "two_layer_rcm_dw", "dw", None),
+        (g_rcm, "global_rcm_dw", "dw", None), (g_none, "global_none_dw", "dw", None),
+        (a_rcm, "atomic_rcm_dw", "dw", None), (a_none, "atomic_none_dw", "dw", None),
+        # FP32 data and arithmetic
+        (part, "two_layer_partition_f32_gather", "f32", "gather"),
+        (part, "two_layer_partition_f32_simple", "f32", "simple"),
+        (part, "two_layer_partition_f32_smem_atomic", "f32", "smem_atomic"),
+        (part, "two_layer_partition_f32_pipelined", "f32", "pipelined"),
+        (rcm, "two_layer_rcm_f32", "f32", None),
+        (part_soa, "two_layer_partition_f32_gather_soa", "f32", "gather"),
+        (g_rcm, "global_rcm_f32", "f32", None), (g_rcm_soa, "global_rcm_f32_soa", "f32", None),
+        (a_rcm, "atomic_rcm_f32", "f32", None), (a_rcm_soa, "atomic_rcm_f32_soa", "f32", None),
+        (t_rcm, "twostep_rcm_f32", "f32", None),
+    ]
+    return v
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=MIN_CALLS,
+                    help="least calls per timed repetition (raised to 100 and to 0.1 s per repetition)")
+    ap.add_argument("--warmup", type=int, default=MIN_WARMUP, help="warm-up calls (at least 10)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--layout", default="aos", choices=["aos", "soa"])
-    ap.add_argument("--staged", default=None, choices=["simple", "gather", "smem_atomic", "pipelined"],
+    ap.add_argument("--staged", default=None, choices=["simple", "gather", "smem_atomic", "pipelined", "warp_agg"],
                     help="increment form of the staged headline kernel (default: the library's)")
-    ap.add_argument("--compute", default="dw", choices=["dw", "f64", "f32"],
-                    help="dw: FP64 data with double-word arithmetic; f64: native FP64; f32: FP32 data")
+    ap.add_argument("--compute", default="f64", choices=["f64", "dw", "f32"],
+                    help="f64: FP64 data and arithmetic (the paper's); dw: FP64 data with double-word "
+                         "arithmetic; f32: FP32 data")
     ap.add_argument("--no-variants", action="store_true", help="skip the baseline variants")
-    ap.add_argument("--rows", default="hex,adjoint,batch,shapes,increment,face",
-                    help="other loops to measure (comma list of hex, adjoint, batch, shapes, increment, face; "
-                         "none for none)")
-    ap.add_argument("--no-rows", action="store_true", help="skip the hex / adjoint / batch measurements")
+    ap.add_argument("--rows", default="hex,adjoint,batch,shapes,increment,face,precision",
+                    help="other loops to measure (comma list of hex, adjoint, batch, shapes, increment, face, "
+                         "precision; none for none)")
+    ap.add_argument("--no-rows", action="store_true", help="skip the other loops")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--nx", type=int, default=NX, help="quad grid size (profiling runs use smaller meshes)")
     ap.add_argument("--ny", type=int, default=NY)
     ap.add_argument("--hex-n", type=int, default=120)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--record-traffic", default=None, metavar="CSV",
+                    help="write the DRAM-traffic record of the headline configuration from an ncu CSV and exit")
+    ap.add_argument("--launches-per-pass", type=int, default=4)
+    ap.add_argument("--record-command", default="", help="the ncu command line the CSV came from")
     args = ap.parse_args()
+    if args.record_traffic:
+        return record_traffic(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -573,64 +833,118 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    timer = Timer(torch, dist)
+    proto = Protocol(torch, dist)
+    warmup = max(args.warmup, MIN_WARMUP)
 
     m = meshgen.quad_mesh(args.nx, args.ny)
     q = meshgen.quad_state(m.ncell)
     adt = synthetic_adt(m)
-    f32 = args.compute == "f32"
-    tdt = torch.float32 if f32 else torch.float64
-    elt = 4 if f32 else 8
-    compute = "dw" if args.compute == "dw" else None
-    useful = useful_bytes_res_calc(m.ncell, m.nnode, m.nedge, elt)
     hbm_peak, peak_kind = read_peaks()
 
-    def setup(coloring, reorder, layout=args.layout, bs=args.block_size, staged=None, recolor=-1):
+    # ------------------------------------------------- CPU baseline (oracle)
+    # rank 0 only, before any GPU work; the oracle's result is the expected
+    # value of every error figure reported below
+    cpu, ref, ref32 = None, None, None
+    if rank == 0 and args.cpu_seconds > 0:
+        r, n, dt, ref = oracle_leg(m, q, adt, args.cpu_seconds)
+        cpu = {"value": r, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} full FP64 res_calc passes of the same mesh ({m.nedge} edges), {dt:.1f} s on 1 core"}
+        ref32 = oracle_res_f32_inputs(m, q, adt)
+
+    tdt_of = {"f64": torch.float64, "dw": torch.float64, "f32": torch.float32}
+    elt_of = {"f64": 8, "dw": 8, "f32": 4}
+
+    def make_plan(coloring, reorder, layout=args.layout, first_fit=False, staged=None):
         P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                         block_size=bs, reorder=reorder, coloring=coloring, layout=layout, staged=staged,
-                         recolor=recolor)
+                         block_size=args.block_size, reorder=reorder, coloring=coloring, layout=layout,
+                         staged=staged, recolor=0 if first_fit else -1)
         P.res.upload()
+        return P
+
+    def make_data(P, compute):
+        tdt = tdt_of[compute]
         d = {"x": torch.tensor(P.to_plan(m.x, "node"), dtype=tdt, device="cuda"),
              "q": torch.tensor(P.to_plan(q, "cell"), dtype=tdt, device="cuda"),
              "adt": torch.tensor(P.to_plan(adt, "cell"), dtype=tdt, device="cuda")}
         d["res"] = torch.zeros_like(d["q"])
-        return P, d
+        return d
+
+    def caller(P, d, compute):
+        comp = "dw" if compute == "dw" else None
+        return lambda: ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS, compute=comp)
+
+    def parity(P, d, fn, compute):
+        """One call on a zeroed res, compared with the oracle (FP32: with the
+        oracle on the FP32-rounded inputs, and with the exact inputs)."""
+        if ref is None:
+            return None
+        d["res"].zero_()
+        fn()
+        torch.cuda.synchronize()
+        got = P.from_plan(d["res"].double().cpu().numpy(), "cell", 4)
+        if compute == "f32":
+            e = field_errors(got, ref32)
+            e["against"] = "FP64 oracle on the FP32-rounded inputs"
+            e["vs_exact_inputs"] = field_errors(got, ref)
+        else:
+            e = field_errors(got, ref)
+            e["against"] = "FP64 oracle, same inputs"
+        return e
+
+    def measure(fn):
+        calls = proto.calls_for(fn, max(args.steps, MIN_CALLS), warmup)
+        ms, reps, win = proto.warm(fn, calls, REPS)
+        msf, repsf, winf = proto.flushed(fn, calls, REPS)
+        return calls, ms, reps, msf, repsf, (win[0], winf[1])
 
     # ---------------------------------------------------------- headline
-    P, d = setup("hier", "partition", staged=args.staged)
+    compute = args.compute
+    elt = elt_of[compute]
+    useful = useful_bytes_res_calc(m.ncell, m.nnode, m.nedge, elt)
+    head_staged = args.staged or default_staged(compute)
+    P = make_plan("hier", "partition")
+    P.res.set_staged(head_staged)
     st = P.res.stats()
-    step = lambda: ml.loop_res_calc(P.res, d["x"], d["q"], d["adt"], d["res"], GAM, EPS, compute=compute)
+    d = make_data(P, compute)
+    step = caller(P, d, compute)
     clk = ClockSampler(local)
     clk.start()
-    ms_step, (t0, t1) = timer(step, args.steps, args.warmup)
+    calls, ms_step, reps_warm, ms_flushed, reps_flushed, (t0, t1) = measure(step)
     clocks = clk.window(t0, t1)
+    head_parity = parity(P, d, step, compute)
     value = job_rate(m.nedge, world, ms_step) / 1e9
     gbs = useful / (ms_step * 1e-3) / 1e9
-    if args.compute == "f64":
+    if compute == "f64":
         roof = {"bound": "alu", "achieved": FLOPS_PER_EDGE * m.nedge / ms_step / 1e9, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_kind": "derived FP64 FMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
-    elif args.compute == "dw":
-        roof = {"bound": "alu", "achieved": FLOPS_PER_EDGE * m.nedge / ms_step / 1e9, "peak": DW_PEAK_TFLOPS,
                 "unit": "TFLOP/s",
-                "peak_kind": "derived double-word rate: FP32 issue (152 SMs x 128 lanes x 2.07 GHz) / "
-                             f"{DW_FP32_OPS_PER_OP} FP32 operations per double-word operation; "
-                             f"FP64-equivalent flops (the FP64 pipe's own peak is {FP64_PEAK_TFLOPS:.3f})"}
+                "peak_kind": "derived FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (1.2 TFLOP/s measured "
+                             "by an FMA probe); achieved = the oracle's 73 flops per edge (each add, multiply "
+                             "counted once) / time"}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                "peak_kind": f"{peak_kind} copy bandwidth (burst)"}
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)"
+                             + ("; the double-word kernel is FP32-issue bound" if compute == "dw" else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    head_staged = args.staged or ("simple" if args.compute == "f64" else "gather")
-    roof["traffic"] = headline_traffic(args, head_staged)
-    roof["traffic_scope"] = "DRAM bytes per pass (all block-colour launches), as achieved; ncu capture"
     roof["useful_bytes"] = useful
-    # the data reuse measure of the plan: useful bytes / DRAM bytes per pass
-    roof["useful_over_dram"] = useful / roof["traffic"] if roof["traffic"] else None
+    roof["useful_frac_hbm"] = gbs / hbm_peak
+    tr, why = read_traffic(compute, head_staged, args)
+    roof["traffic"] = tr["bytes_per_pass"] if tr else None
+    roof["traffic_source"] = why
+    roof["traffic_scope"] = ("DRAM bytes (read + write) per pass of 4 block-colour launches, ncu "
+                             "--cache-control none over consecutive passes")
+    if tr:
+        roof["traffic_read"] = tr["read_bytes_per_pass"]
+        roof["traffic_write"] = tr["write_bytes_per_pass"]
+        # the data reuse measure of the plan: useful bytes / DRAM bytes per pass
+        roof["useful_over_dram"] = useful / tr["bytes_per_pass"]
+        roof["achieved_dram_gbs"] = tr["bytes_per_pass"] / (ms_step * 1e-3) / 1e9
 
     # ---------------------------------------------------------- e2e (host buffers)
     # through the C-ABI call with host arrays (loop_res_calc_host): every step
     # copies its inputs from pinned host memory and reads res back; steps
     # alternate two streams and two sets of host arrays, so one step's copies
     # overlap the other's loop
+    tdt = tdt_of[compute]
     hsets = []
     for _ in range(2):
         hsets.append([torch.tensor(P.to_plan(m.x, "node"), dtype=tdt).pin_memory(),
@@ -639,92 +953,95 @@ def main():
                       torch.zeros((m.ncell, 4), dtype=tdt).pin_memory()])
     e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     e2e_k = [0]
+    comp = "dw" if compute == "dw" else None
 
     def e2e_step():
         k = e2e_k[0]
         e2e_k[0] += 1
-        ml.loop_res_calc_host(P.res, *hsets[k % 2], GAM, EPS, stream=e2e_streams[k % 2], compute=compute)
+        ml.loop_res_calc_host(P.res, *hsets[k % 2], GAM, EPS, stream=e2e_streams[k % 2], compute=comp)
 
-    def e2e_timed(n, w):
-        for _ in range(w):
-            e2e_step()
+    def e2e_rep(n):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        if dist is not None:
+            dist.barrier()
+        t = time.perf_counter()
         for _ in range(n):
             e2e_step()
         torch.cuda.synchronize()
-        return (time.perf_counter() - t0) * 1e3 / n
+        return (time.perf_counter() - t) * 1e3 / n
 
-    e2e_ms = e2e_timed(max(4, min(args.steps, 20)), 3)
+    for _ in range(3):
+        e2e_step()
+    e2e_ms = float(np.median(max_over_ranks([e2e_rep(20) for _ in range(3)], dist, "cuda")))
     h2d = sum(t.numel() for t in hsets[0]) * elt
     d2h = hsets[0][3].numel() * elt
-    launches = args.steps * st["nblock_colors"]
-    del d
+    launches = 2 * REPS * calls * st["nblock_colors"]
+    del d, hsets
 
     # ---------------------------------------------------------- variants
-    head_name = "two_layer_partition" + ("_dw" if compute else "") + f"_{head_staged}"
+    head_name = f"two_layer_partition_{compute}_{head_staged}"
     variants = {head_name: {
-        "gedges_s": value / world, "ms": ms_step, "useful_gbs": gbs, "block_colors": st["nblock_colors"],
-        "thread_colors_mean": st["mean_thread_colors"], "reuse": st["reuse_all"],
-        "plan_seconds": st["seconds_total"]}}
+        "gedges_s": value / world, "ms": ms_step, "ms_flushed": ms_flushed, "useful_gbs": gbs,
+        "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
+        "reuse": st["reuse_all"], "plan_seconds": st["seconds_total"], "parity": head_parity}}
     if not args.no_variants:
-        ks = max(5, args.steps // 2)
-        other = "gather" if head_staged != "gather" else "simple"
-        todo = [("two_layer_partition" + ("_dw" if compute else "") + f"_{other}", "hier", "partition",
-                 compute, other),
-                ("two_layer_partition" + ("_dw" if compute else "") + "_first_fit_colours", "hier", "partition",
-                 compute, args.staged, 0),
-                ("two_layer_rcm", "hier", "rcm", compute, args.staged), ("global_rcm", "global", "rcm", None, None),
-                ("global_none", "global", "none", None, None), ("atomic_rcm", "atomic", "rcm", None, None),
-                ("atomic_none", "atomic", "none", None, None), ("twostep_rcm", "twostep", "rcm", None, None)]
-        pre = "two_layer_partition_" + ("native_f64_" if compute else "")
-        todo += [(pre + "smem_atomic", "hier", "partition", None, "smem_atomic"),
-                 (pre + "warp_agg", "hier", "partition", None, "warp_agg")]
-        if compute == "dw":
-            todo.insert(1, ("two_layer_partition_native_f64", "hier", "partition", None, None))
-            todo.insert(2, ("two_layer_partition_native_f64_gather", "hier", "partition", None, "gather"))
-        for name, coloring, reorder, comp, stg, *rc in todo:
+        plans = {("hier", "partition", args.layout, False): P}
+        for key, name, comp_v, staged in res_variants(compute):
+            if name == head_name and key == ("hier", "partition", args.layout, False):
+                continue
             try:
-                Pv, dv = setup(coloring, reorder, staged=stg, recolor=rc[0] if rc else -1)
+                if key not in plans:
+                    plans.clear()   # plans are visited grouped: free the previous one
+                    plans[key] = make_plan(key[0], key[1], layout=key[2], first_fit=key[3])
+                Pv = plans[key]
+                if key[0] == "hier":
+                    Pv.res.set_staged(staged)
+                dv = make_data(Pv, comp_v)
+                fn = caller(Pv, dv, comp_v)
+                n_v, msv, _, msfv, _, _ = measure(fn)
             except ml.MeshLoopError as e:
                 variants[name] = {"error": str(e)}
                 continue
-            fn = lambda: ml.loop_res_calc(Pv.res, dv["x"], dv["q"], dv["adt"], dv["res"], GAM, EPS, compute=comp)
-            msv, _ = timer(fn, ks, 2)
-            variants[name] = {"gedges_s": m.nedge / msv / 1e6, "ms": msv, "useful_gbs": useful / msv / 1e6,
-                              "colors": Pv.res.stats()["nblock_colors"]}
-            del dv, Pv
+            u = useful_bytes_res_calc(m.ncell, m.nnode, m.nedge, elt_of[comp_v])
+            variants[name] = {"gedges_s": m.nedge / msv / 1e6, "ms": msv, "ms_flushed": msfv,
+                              "useful_gbs": u / msv / 1e6, "frac_hbm": u / msv / 1e6 / hbm_peak,
+                              "colors": Pv.res.stats()["nblock_colors"], "calls_per_rep": n_v,
+                              "parity": parity(Pv, dv, fn, comp_v)}
+            del dv
+        plans.clear()
+    del P
 
-    rows = None if args.no_rows else bench_rows(ml, torch, timer, args)
+    rows = None if args.no_rows else bench_rows(ml, torch, proto, args)
     clk.stop()
 
-    # ---------------------------------------------------------- CPU baseline (oracle)
-    cpu = None
-    if rank == 0 and args.cpu_seconds > 0:
-        r, n, dt = oracle_res_calc_rate(m, q, adt, args.cpu_seconds)
-        cpu = {"value": r, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} full FP64 res_calc passes of the same mesh ({m.nedge} edges), {dt:.1f} s on 1 core"}
-
     if rank == 0:
-        dtype = {"dw": "f64dw", "f64": "f64", "f32": "f32"}[args.compute]
+        dtype = {"dw": "f64dw", "f64": "f64", "f32": "f32"}[compute]
         line = {
-            "metric": METRIC, "value": value, "unit": "Gedges/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": value, "unit": "Gedges/s", "n_gpus": world, "steps": calls,
+            "warmup": warmup, "reps": REPS, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": f"res_calc {args.nx}x{args.ny} jittered renumbered quads, "
-                                   + ("FP32 data" if f32 else "FP64 data"),
+                                   + {"f64": "FP64 data and arithmetic", "dw": "FP64 data, double-word arithmetic",
+                                      "f32": "FP32 data and arithmetic"}[compute],
                        "cells": m.ncell, "nodes": m.nnode, "edges": m.nedge,
-                       "implementation": ("double-word arithmetic, " if compute else "")
-                                         + f"two-layer colouring"
+                       "implementation": ("double-word arithmetic, " if compute == "dw" else "")
+                                         + "two-layer colouring"
                                          + f" ({'thread-coloured' if head_staged == 'simple' else head_staged}"
                                          + f" increments), RCM + partition, block {args.block_size}, "
                                          + args.layout.upper(),
                        "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 (useful bytes {useful / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB)"},
-            "useful_gbs": gbs, "useful_frac_hbm": gbs / hbm_peak,
+                       "l2": f"inputs larger than L2 (useful bytes {useful / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB); "
+                             "value from the warm regime, the L2-flushed regime (a 258 MB write before every "
+                             "call) in timing"},
+            "timing": {"protocol": f"{warmup} warm-up calls; {REPS} repetitions of {calls} calls; median; "
+                                   "CUDA events on the launching stream",
+                       "warm_ms_median": ms_step, "warm_ms_reps": reps_warm,
+                       "flushed_ms_median": ms_flushed, "flushed_ms_reps": reps_flushed,
+                       "flushed_gedges_s": m.nedge / ms_flushed / 1e6},
+            "useful_gbs": gbs, "useful_frac_hbm": gbs / hbm_peak, "parity": head_parity,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * m.nedge / e2e_ms / 1e6, "unit": "Gedges/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": launches, "clocks": clocks,
             "plan": {"blocks": st["nblocks"], "block_colors": st["nblock_colors"],
                      "thread_colors_max": st["max_thread_colors"], "reuse": st["reuse_all"],

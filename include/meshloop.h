@@ -83,11 +83,17 @@ enum { MP_COLOR_HIER = 0, MP_COLOR_GLOBAL = 1, MP_COLOR_ATOMIC = 2, MP_COLOR_TWO
 enum { MP_LAYOUT_AOS = 0, MP_LAYOUT_SOA = 1 };
 enum { MP_F64 = 0, MP_F32 = 1, MP_F64_DW = 2 };
 /* MP_F64_DW: FP64 data, arithmetic in double-word (pairs of FP32, ~48-bit
- * significand) on the FP32 pipes; results agree with FP64 to ~1e-13
- * relative.  Offered by loop_res_calc, loop_adjoint, loop_elem_assemble and
- * loop_face_flux with HIER plans (res_calc and hex assembly: gather
- * increments by default, MP_STAGED_SIMPLE for thread colours; hex: blocks
- * of at most 256 threads; face flux: at most 128).                       */
+ * significand, FP32's exponent range) on the FP32 pipes; results agree with
+ * FP64 to ~1e-13 relative while the values the loop forms (inputs, their
+ * products and the fluxes) stay within about 1e-30..1e38 in magnitude:
+ * zeros are exact, smaller values lose relative precision gradually
+ * (subnormal FP32 low parts), larger ones overflow.  Offered by
+ * loop_res_calc, loop_adjoint, loop_elem_assemble and loop_face_flux with
+ * HIER plans (res_calc and hex assembly: gather increments by default,
+ * MP_STAGED_SIMPLE for thread colours; hex: blocks of at most 256 threads;
+ * face flux: at most 128), and by loop_res_calc and loop_elem_assemble with
+ * GLOBAL and ATOMIC plans (the Sec. 2.1 baselines in the same arithmetic:
+ * FP64 read-add-write of res / f per colour, or FP64 atomicAdd).          */
 
 /* One map of the loop: from the loop's iteration set (set id 0) to the
  * caller's set `to_set` (ids >= 1; maps with the same id share a to-set).
@@ -172,11 +178,21 @@ typedef struct {
  * Errors: MP_EINVAL, MP_EMAPRANGE, MP_ECOLORS, MP_ENOMEM.                */
 int mesh_plan_build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_opts *opts,
                     mp_plan **out);
+/* Free a plan and its device tables (NULL is a no-op).  The plan is the
+ * reusable product of the one-off reordering and colouring (Sec. 2.3.2);
+ * it must not be in use by a loop call still queued on a stream.        */
 void mesh_plan_destroy(mp_plan *plan);
+/* Plan statistics (Sec. 3.1's block counts, colour counts and data reuse).
+ * Errors: MP_EINVAL (null argument).                                    */
 int mesh_plan_query(const mp_plan *plan, mp_plan_stats *stats);
 
 /* new_to_old permutation of set `set_id` (0 = the from-set, else a to-set
- * id of the maps): new_to_old[new] = old, length = the set's size.        */
+ * id of the maps): new_to_old[new] = old, length = the set's size.  The
+ * renumbering of Sec. 2.3.1 (reordering of the primary to-set and the
+ * iterations) and Sec. 2.3.2 (data points by accessing blocks): callers
+ * move their data into plan numbering with it.  new_to_old is host memory
+ * of the set's size, owned by the caller.  Errors: MP_EINVAL (null
+ * argument or unknown set id).                                           */
 int mesh_plan_perm(const mp_plan *plan, int32_t set_id, int32_t *new_to_old);
 
 /* Copy one host plan table into out (capacity `cap` elements of the
@@ -340,11 +356,14 @@ int loop_update(int64_t ncell, int32_t dtype, int32_t layout, const void *qold, 
                 const void *adt, double *rms_dev, void *stream);
 
 /* Allocation-free variant of loop_update (the paper has no counterpart).
- * Same arguments, results and determinism as loop_update, but its scratch
- * (one FP64 partial sum per CTA of 256 threads) is a fixed static device
- * array of MP_NOALLOC_MAX_PARTIALS doubles inside the library instead of
- * memory obtained from cudaMalloc, so the call never allocates or frees
- * device memory.  It is meant for callers that cannot allocate: host
+ * Same arguments as loop_update, and the same q and res bit for bit; the
+ * residual sum is deterministic from run to run, but its partial sums are
+ * grouped differently from loop_update's (one per CTA of 2048 cells), so
+ * it may differ from loop_update's in the last bits.  Its scratch (one FP64
+ * partial sum per CTA) is a fixed static device array of
+ * MP_NOALLOC_MAX_PARTIALS doubles inside the library instead of memory
+ * obtained from cudaMalloc, so the call never allocates or frees device
+ * memory.  It is meant for callers that cannot allocate: host
  * applications that reserve all device memory up front in their own pool,
  * or that forbid device allocation (and the implicit device synchronisation
  * cudaMalloc may cause) once they are running.
@@ -353,7 +372,9 @@ int loop_update(int64_t ncell, int32_t dtype, int32_t layout, const void *qold, 
  *    larger sizes return MP_ETOOBIG before anything is launched.
  *  - The first call on each device looks up the device address of the
  *    static array (cudaGetSymbolAddress) with that device current; make that
- *    first call before any stream capture.
+ *    first call before any stream capture.  The address is kept for the
+ *    life of the process: do not reset the device's primary context
+ *    (cudaDeviceReset) after that first call.
  *  - Every device that loads the library holds the array until exit.  All
  *    calls share it and it keeps the last call's partial sums; each call
  *    overwrites every entry it reads, so nothing needs clearing, but calls
@@ -385,7 +406,7 @@ int loop_adjoint(const mp_plan *plan, int32_t dtype, const void *x, const void *
                  void *stream);
 
 /* Increment-only edge loop with the access pattern of Volna's
- * SpaceDiscretization (Sec. 3.1.3): per edge 7 values and 1 integer read
+ * SpaceDiscretization (Sec. 3.1.2): per edge 7 values and 1 integer read
  * directly, per cell 1 value read and 4 incremented.  With the edge's
  * direct data d = (F0, F1, F2, P, L, nx, ny) (flux, pressure, length, unit
  * normal out of its first cell):
@@ -406,7 +427,7 @@ int loop_space_disc(const mp_plan *plan, int32_t dtype, const void *edata, const
                     const void *inv_area, void *res, void *stream);
 
 /* Increment-only cell loop with the access pattern of BookLeaf's
- * getacc_scatter (Sec. 3.1.4): per cell 17 values read directly,
+ * getacc_scatter (Sec. 3.1.3): per cell 17 values read directly,
  * (rho, m[4], w[4], fx[4], fy[4]); node k of the cell (cell->node order) gets
  *   nd[n_k] += (m_k, rho w_k, fx_k, fy_k).
  * Plan: maps {cell->node (4, written)}; HIER (block size <= 512; gather
@@ -442,9 +463,16 @@ int loop_face_flux(const mp_plan *plan, int32_t dtype, const void *fdata, const 
                    double gam, double mu, double pr, void *stream);
 
 /* --------------------------------------------------------------- status */
+/* Name and meaning of an MP_* code (a static string; unknown codes give
+ * "unknown error").  The codes include the failure modes of Sec. 3.1.5:
+ * MP_ECOLORS (the 256-colour limit) and MP_ESMEM (a block footprint that
+ * does not fit shared memory).                                          */
 const char *mp_error_string(int code);
-/* Reads (and clears) the device error word of the library's bounded waits:
- * MP_OK or MP_ETIMEOUT.  Synchronises the stream.                       */
+/* Reads (and clears) the library's device error word, where kernels record
+ * what they detect while running: MP_OK, MP_ESMEM (a staged kernel found
+ * its shared-memory carve-up or its block's footprint larger than the
+ * launch provides, and returned without touching memory) or MP_ETIMEOUT (a
+ * bounded device-side wait gave up).  Synchronises the stream.          */
 int mp_check_device_status(void *stream);
 /* Library version string. */
 const char *mp_version(void);

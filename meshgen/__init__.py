@@ -30,7 +30,7 @@ Meshes (Sec. 1.1 of the paper: sets, fixed-arity maps and data on sets):
   cell c1 (the triangle that lists the edge's nodes counter-clockwise) and
   c2 = the neighbour, or c2 = c1 with flag 1 on the boundary.
 * ``volna_fields`` / ``bookleaf_fields`` -- direct data of the increment-only
-  loops (Sec. 3.1.3 and 3.1.4): per edge 7 floats and 1 integer, per cell 17
+  loops (Sec. 3.1.2 and 3.1.3): per edge 7 floats and 1 integer, per cell 17
   doubles.
 * ``hex_faces(mesh, dims)`` / ``aero_cells(mesh)`` -- the interior faces of a
   structured hex grid (face->cell[2], from the cell on the low side to the

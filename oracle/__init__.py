@@ -217,7 +217,7 @@ def res_calc_cstep(edge2node, edge2cell, x, dx, q, dq, adt, h=1e-30, gam=GAMMA, 
 
 
 def space_disc(edge2cell, edata, eflag, inv_area, res=None):
-    """Volna-style increment-only edge loop (Sec. 3.1.3); res [ncell, 4] +=."""
+    """Volna-style increment-only edge loop (Sec. 3.1.2); res [ncell, 4] +=."""
     e2c, pe = _i32(edge2cell)
     _, pd = _f64(edata)
     _, pf = _i32(eflag)
@@ -228,7 +228,7 @@ def space_disc(edge2cell, edata, eflag, inv_area, res=None):
 
 
 def getacc(cell2node, cdata, nnode, nd=None):
-    """BookLeaf-style increment-only cell loop (Sec. 3.1.4); nd [nnode, 4] +=."""
+    """BookLeaf-style increment-only cell loop (Sec. 3.1.3); nd [nnode, 4] +=."""
     c2n, pc = _i32(cell2node)
     _, pd = _f64(cdata)
     out = np.zeros((nnode, 4)) if nd is None else np.array(nd, dtype=np.float64)

@@ -25,7 +25,7 @@
  *              plus Flanagan-Belytschko hourglass control.
  *   adjoint    reverse-mode derivative of res_calc in q and x (adt fixed).
  *   space_disc an increment-only edge loop with the access pattern of
- *              Volna's SpaceDiscretization (Sec. 3.1.3: per edge 7 floats
+ *              Volna's SpaceDiscretization (Sec. 3.1.2: per edge 7 floats
  *              and 1 integer read directly, 1 value read and 4 incremented
  *              on each of 2 cells): the flux through the edge, already
  *              given per edge, integrated over its length, plus a pressure
@@ -37,7 +37,7 @@
  *              (local Lax-Friedrichs) flux of the 3D Euler equations, and a
  *              Newtonian viscous and heat flux from face gradients.
  *   getacc     an increment-only cell loop with the access pattern of
- *              BookLeaf's getacc_scatter (Sec. 3.1.4: 17 doubles read
+ *              BookLeaf's getacc_scatter (Sec. 3.1.3: 17 doubles read
  *              directly per cell, 4 incremented on each of 4 nodes): the
  *              cell's corner mass, density-weighted corner area and corner
  *              forces gathered onto the nodes.
@@ -405,7 +405,7 @@ void oracle_res_calc_cstep(int64_t ncell, int64_t nedge, const int32_t *edge2nod
 
 /* ------------------------------------------------------ increment-only loops */
 
-/* Volna-style edge loop (Sec. 3.1.3).  Per edge e with cells (c1, c2),
+/* Volna-style edge loop (Sec. 3.1.2).  Per edge e with cells (c1, c2),
  * direct data d = (F0, F1, F2, P, L, nx, ny) and flag:
  *   w = L (F0, F1 + P nx, F2 + P ny, P)
  *   res[c1] -= inv_area[c1] w;   res[c2] += inv_area[c2] w   unless flag
@@ -424,7 +424,7 @@ void oracle_space_disc(int64_t nedge, const int32_t *edge2cell, const double *ed
     }
 }
 
-/* BookLeaf-style cell loop (Sec. 3.1.4).  Per cell c with nodes n0..n3 and
+/* BookLeaf-style cell loop (Sec. 3.1.3).  Per cell c with nodes n0..n3 and
  * direct data (rho, m[4], w[4], fx[4], fy[4]):
  *   nd[n_k] += (m_k, rho w_k, fx_k, fy_k),  k = 0..3 */
 void oracle_getacc(int64_t ncell, const int32_t *cell2node, const double *cdata, double *nd)

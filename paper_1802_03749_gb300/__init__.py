@@ -404,7 +404,7 @@ def loop_adjoint(plan: Plan, x, q, adt, res_bar, q_bar, x_bar, gam: float = 1.4,
 
 
 def loop_space_disc(plan: Plan, edata, eflag, inv_area, res, stream=None):
-    """Increment-only edge loop (Volna-style, Sec. 3.1.3); res +=."""
+    """Increment-only edge loop (Volna-style, Sec. 3.1.2); res +=."""
     import torch
     dt = _dtype_of(edata, inv_area, res)
     if eflag.dtype != torch.int32 or not eflag.is_cuda or not eflag.is_contiguous():
@@ -414,7 +414,7 @@ def loop_space_disc(plan: Plan, edata, eflag, inv_area, res, stream=None):
 
 
 def loop_getacc(plan: Plan, cdata, nd, stream=None):
-    """Increment-only cell loop (BookLeaf-style, Sec. 3.1.4); nd +=."""
+    """Increment-only cell loop (BookLeaf-style, Sec. 3.1.3); nd +=."""
     dt = _dtype_of(cdata, nd)
     _check(lib().loop_getacc(plan.handle, dt, _ptr(cdata), _ptr(nd), _stream(stream)), "loop_getacc")
 

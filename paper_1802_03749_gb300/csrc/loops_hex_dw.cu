@@ -11,6 +11,8 @@
 // each footprint node's f is written back once
 // (FP64 + double-word, two FP64 additions).  Element volumes are written
 // directly.  The formulas are those of the FP64 kernel (loops_hex.cu).
+// GLOBAL and ATOMIC plans run the baselines of Sec. 2.1 in the same
+// arithmetic (hex_direct_dw).
 #include "common.cuh"
 #include "dw.cuh"
 
@@ -62,6 +64,98 @@ __device__ __forceinline__ void corner_force(int i, const dw t[3][3], const dw w
         dw_dot_add(H, gi[2], qk[2][a]);
         dw_dot_add(H, gi[3], qk[3][a]);
         fa[a] = dw_add_fast(st, dw_neg(dw_dot_end(H)));
+    }
+}
+
+// The element quantities that the corner forces need, in double-word
+// arithmetic, from accessors X(a, i), Vel(a, i) (component a of corner i's
+// coordinates and velocity) and Sig(a) (the element's stress component a);
+// Vol(V) receives the volume V = 8 det J as soon as it is known.
+// With C = cof(J) and B_i = C xi_i:
+//   stress   f_i[a] = -s_a B_i[a] = sum_b xi_i[b] t[a][b],  t[a][b] = -s_a C[a][b]
+//   hourglass g_{k,i} = Gamma_{k,i} - (xi_i . w_k) / V,    w_k[b] = sum_a h_k[a] C[a][b]
+//            q_k = kappa sum_j g_{k,j} v_j,  f_i -= sum_k g_{k,i} q_k
+// so only t, w and q (not the 8 B_i) are kept between the two phases;
+// iV = 1/V.
+template <typename FX, typename FV, typename FS, typename FW>
+__device__ __forceinline__ void hex_terms_dw(FX X, FV Vel, FS Sig, FW Vol, dw kappa, dw t[3][3], dw w[4][3],
+                                             dw qk[4][3], dw &iV)
+{
+    // J = 1/8 sum_i x_i xi_i^T
+    dw J[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const dw x0 = X(a, 0);
+        dw j0 = sgn(x0, sx(0)), j1 = sgn(x0, sy(0)), j2 = sgn(x0, sz(0));
+#pragma unroll
+        for (int i = 1; i < 8; ++i) {
+            const dw xi = X(a, i);
+            j0 = dw_add_fast(j0, sgn(xi, sx(i)));
+            j1 = dw_add_fast(j1, sgn(xi, sy(i)));
+            j2 = dw_add_fast(j2, sgn(xi, sz(i)));
+        }
+        J[a][0] = dw_scale2(j0, 0.125f);
+        J[a][1] = dw_scale2(j1, 0.125f);
+        J[a][2] = dw_scale2(j2, 0.125f);
+    }
+    dw C[3][3];
+    C[0][0] = dw_det2(J[1][1], J[2][2], J[1][2], J[2][1]);
+    C[0][1] = dw_det2(J[1][2], J[2][0], J[1][0], J[2][2]);
+    C[0][2] = dw_det2(J[1][0], J[2][1], J[1][1], J[2][0]);
+    C[1][0] = dw_det2(J[0][2], J[2][1], J[0][1], J[2][2]);
+    C[1][1] = dw_det2(J[0][0], J[2][2], J[0][2], J[2][0]);
+    C[1][2] = dw_det2(J[0][1], J[2][0], J[0][0], J[2][1]);
+    C[2][0] = dw_det2(J[0][1], J[1][2], J[0][2], J[1][1]);
+    C[2][1] = dw_det2(J[0][2], J[1][0], J[0][0], J[1][2]);
+    C[2][2] = dw_det2(J[0][0], J[1][1], J[0][1], J[1][0]);
+    dw_acc A = dw_dot_begin(J[0][0], C[0][0]);
+    dw_dot_add(A, J[0][1], C[0][1]);
+    dw_dot_add(A, J[0][2], C[0][2]);
+    const dw V = dw_scale2(dw_dot_end(A), 8.0f);
+    Vol(V);
+    iV = dw_recip(V);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const dw sa = Sig(a);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) t[a][b] = dw_neg(dw_mul(sa, C[a][b]));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int G[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            G[j] = k == 0 ? sy(j) * sz(j) : (k == 1 ? sx(j) * sz(j) : (k == 2 ? sx(j) * sy(j) : sx(j) * sy(j) * sz(j)));
+        dw h[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            h[a] = sgn(X(a, 0), G[0]);
+#pragma unroll
+            for (int j = 1; j < 8; ++j) h[a] = dw_add_fast(h[a], sgn(X(a, j), G[j]));
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            dw_acc P = dw_dot_begin(h[0], C[0][b]);
+            dw_dot_add(P, h[1], C[1][b]);
+            dw_dot_add(P, h[2], C[2][b]);
+            w[k][b] = dw_dot_end(P);
+        }
+        dw_acc Q[3];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const dw xb = dw_add_fast(dw_add_fast(sgn(w[k][0], sx(j)), sgn(w[k][1], sy(j))), sgn(w[k][2], sz(j)));
+            const dw gj = dw_add_fast(dw{(float)G[j], 0.f}, dw_neg(dw_mul(xb, iV)));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const dw vj = Vel(a, j);
+                if (j == 0)
+                    Q[a] = dw_dot_begin(gj, vj);
+                else
+                    dw_dot_add(Q[a], gj, vj);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) qk[k][a] = dw_mul(dw_dot_end(Q[a]), kappa);
     }
 }
 
@@ -146,11 +240,7 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
         if (two) load_f(i1, g1);
     }
     __syncthreads();
-    // Per element, with C = cof(J) and B_i = C xi_i:
-    //   stress   f_i[a] = -s_a B_i[a] = sum_b xi_i[b] t[a][b],  t[a][b] = -s_a C[a][b]
-    //   hourglass g_{k,i} = Gamma_{k,i} - (xi_i . w_k) / V,    w_k[b] = sum_a h_k[a] C[a][b]
-    //            q_k = kappa sum_j g_{k,j} v_j,  f_i -= sum_k g_{k,i} q_k
-    // so only t, w and q (not the 8 B_i) are kept between the two phases.
+    // the element's force terms from the staged nodes
     int loc[8];
     dw t[3][3], w[4][3], qk[4][3], iV;
     if (active) {
@@ -163,82 +253,10 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
         loc[5] = l.z >> 16;
         loc[6] = l.w & 0xffff;
         loc[7] = l.w >> 16;
-        // J = 1/8 sum_i x_i xi_i^T
-        dw J[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const dw x0 = ld2(s_x, a * cap + loc[0]);
-            dw j0 = sgn(x0, sx(0)), j1 = sgn(x0, sy(0)), j2 = sgn(x0, sz(0));
-#pragma unroll
-            for (int i = 1; i < 8; ++i) {
-                const dw xi = ld2(s_x, a * cap + loc[i]);
-                j0 = dw_add_fast(j0, sgn(xi, sx(i)));
-                j1 = dw_add_fast(j1, sgn(xi, sy(i)));
-                j2 = dw_add_fast(j2, sgn(xi, sz(i)));
-            }
-            J[a][0] = dw_scale2(j0, 0.125f);
-            J[a][1] = dw_scale2(j1, 0.125f);
-            J[a][2] = dw_scale2(j2, 0.125f);
-        }
-        dw C[3][3];
-        C[0][0] = dw_det2(J[1][1], J[2][2], J[1][2], J[2][1]);
-        C[0][1] = dw_det2(J[1][2], J[2][0], J[1][0], J[2][2]);
-        C[0][2] = dw_det2(J[1][0], J[2][1], J[1][1], J[2][0]);
-        C[1][0] = dw_det2(J[0][2], J[2][1], J[0][1], J[2][2]);
-        C[1][1] = dw_det2(J[0][0], J[2][2], J[0][2], J[2][0]);
-        C[1][2] = dw_det2(J[0][1], J[2][0], J[0][0], J[2][1]);
-        C[2][0] = dw_det2(J[0][1], J[1][2], J[0][2], J[1][1]);
-        C[2][1] = dw_det2(J[0][2], J[1][0], J[0][0], J[1][2]);
-        C[2][2] = dw_det2(J[0][0], J[1][1], J[0][1], J[1][0]);
-        dw_acc A = dw_dot_begin(J[0][0], C[0][0]);
-        dw_dot_add(A, J[0][1], C[0][1]);
-        dw_dot_add(A, J[0][2], C[0][2]);
-        const dw V = dw_scale2(dw_dot_end(A), 8.0f);
-        vol[e] = dw_to_double(V);
-        iV = dw_recip(V);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const dw sa = dw_from_double_int(SOA ? sig[a * nelem + e] : sig[3 * (int64_t)e + a]);
-#pragma unroll
-            for (int b = 0; b < 3; ++b) t[a][b] = dw_neg(dw_mul(sa, C[a][b]));
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int G[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                G[j] = k == 0 ? sy(j) * sz(j) : (k == 1 ? sx(j) * sz(j) : (k == 2 ? sx(j) * sy(j) : sx(j) * sy(j) * sz(j)));
-            dw h[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                h[a] = sgn(ld2(s_x, a * cap + loc[0]), G[0]);
-#pragma unroll
-                for (int j = 1; j < 8; ++j) h[a] = dw_add_fast(h[a], sgn(ld2(s_x, a * cap + loc[j]), G[j]));
-            }
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                dw_acc P = dw_dot_begin(h[0], C[0][b]);
-                dw_dot_add(P, h[1], C[1][b]);
-                dw_dot_add(P, h[2], C[2][b]);
-                w[k][b] = dw_dot_end(P);
-            }
-            dw_acc Q[3];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const dw xb = dw_add_fast(dw_add_fast(sgn(w[k][0], sx(j)), sgn(w[k][1], sy(j))), sgn(w[k][2], sz(j)));
-                const dw gj = dw_add_fast(dw{(float)G[j], 0.f}, dw_neg(dw_mul(xb, iV)));
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const dw vj = ld2(s_v, a * cap + loc[j]);
-                    if (j == 0)
-                        Q[a] = dw_dot_begin(gj, vj);
-                    else
-                        dw_dot_add(Q[a], gj, vj);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) qk[k][a] = dw_mul(dw_dot_end(Q[a]), kappa);
-        }
+        hex_terms_dw([&](int a, int i) { return ld2(s_x, a * cap + loc[i]); },
+                     [&](int a, int i) { return ld2(s_v, a * cap + loc[i]); },
+                     [&](int a) { return dw_from_double_int(SOA ? sig[a * nelem + e] : sig[3 * (int64_t)e + a]); },
+                     [&](dw V) { vol[e] = dw_to_double(V); }, kappa, t, w, qk, iV);
     }
     if constexpr (GATHER) {
         // every thread writes its 24 corner forces at once, then each node
@@ -299,6 +317,88 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
     }
 }
 
+// The baselines of Sec. 2.1 in the same double-word arithmetic, so that the
+// strategies compare at equal arithmetic: one thread per element of
+// [e0, e1) gathers its 8 nodes' x and v from global memory (FP64), converts
+// them into its own slice of shared memory (private scratch: no thread reads
+// another's), computes the element as the staged kernel does, writes vol and
+// adds its 24 corner forces to f:
+//   GLOBAL (elements of one colour share no node): f = f + fa in FP64 (two
+//          FP64 additions, as the staged write-back);
+//   ATOMIC: atomicAdd of the nearest double of fa (hi + lo, one FP64
+//          addition).
+constexpr int kHexDirectDwBlock = 128;
+constexpr int kHexDirectDwSmem = 48 * 8 * kHexDirectDwBlock;  // x, v of 8 corners as double-words
+
+template <bool SOA, bool ATOMIC>
+__global__ void __launch_bounds__(kHexDirectDwBlock) hex_direct_dw(int e0, int e1, const int32_t *__restrict__ e2n,
+                                                                  const double *__restrict__ x,
+                                                                  const double *__restrict__ v,
+                                                                  const double *__restrict__ sig,
+                                                                  double *__restrict__ f, double *__restrict__ vol,
+                                                                  int64_t nnode, int64_t nelem, dw kappa)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *s_xv = reinterpret_cast<float2 *>(smem_raw);  // [48][blockDim]: x, then v, component-major
+    mp_pdl_trigger();
+    const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;  // no barrier below: threads past the end leave
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int4 na = reinterpret_cast<const int4 *>(e2n)[2 * (int64_t)e];
+    const int4 nb = reinterpret_cast<const int4 *>(e2n)[2 * (int64_t)e + 1];
+    const int nd[8] = {na.x, na.y, na.z, na.w, nb.x, nb.y, nb.z, nb.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t j = SOA ? a * nnode + nd[i] : 3 * (int64_t)nd[i] + a;
+            st2(s_xv, (a * 8 + i) * nt + tid, dw_from_double_int(x[j]));
+            st2(s_xv, (24 + a * 8 + i) * nt + tid, dw_from_double_int(v[j]));
+        }
+    }
+    dw t[3][3], w[4][3], qk[4][3], iV;
+    hex_terms_dw([&](int a, int i) { return ld2(s_xv, (a * 8 + i) * nt + tid); },
+                 [&](int a, int i) { return ld2(s_xv, (24 + a * 8 + i) * nt + tid); },
+                 [&](int a) { return dw_from_double_int(SOA ? sig[a * nelem + e] : sig[3 * (int64_t)e + a]); },
+                 [&](dw V) { vol[e] = dw_to_double(V); }, kappa, t, w, qk, iV);
+    if (!ATOMIC) mp_pdl_wait();  // f: read-add-written by the previous colour's launch
+#pragma unroll 1
+    for (int i = 0; i < 8; ++i) {
+        dw fa[3];
+        corner_force(i, t, w, qk, iV, fa);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t j = SOA ? a * nnode + nd[i] : 3 * (int64_t)nd[i] + a;
+            if (ATOMIC)
+                atomicAdd(f + j, f32_to_f64_int(fa[a].hi) + f32_to_f64_int(fa[a].lo));
+            else
+                f[j] = f64_add_dw(f[j], fa[a]);
+        }
+    }
+}
+
+template <bool SOA>
+int hex_direct_dw_t(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, dw kap,
+                    cudaStream_t s)
+{
+    const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;
+    auto kern = atomic ? hex_direct_dw<SOA, true> : hex_direct_dw<SOA, false>;
+    int rc = mp_allow_smem(kern, kHexDirectDwSmem);
+    if (rc != MP_OK) return rc;
+    bool overlap = false;
+    for (int c = 0; c < P->ncolors; ++c) {
+        const int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
+        if (e1 <= e0) continue;
+        MP_CUDA_TRY(mp_launch(kern, (e1 - e0 + kHexDirectDwBlock - 1) / kHexDirectDwBlock, kHexDirectDwBlock,
+                              kHexDirectDwSmem, s, overlap && !atomic, e0, e1, P->dev.map[0], (const double *)x,
+                              (const double *)v, (const double *)sig, (double *)f, (double *)vol, P->maps[0].to_size,
+                              P->from_size, kap));
+        overlap = true;
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
 template <bool SOA>
 int hex_dw_t(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, double kappa,
              cudaStream_t s)
@@ -334,7 +434,14 @@ int hex_dw_t(const mp_plan *P, const void *x, const void *v, const void *sig, vo
 int mp_hex_dw(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol, double kappa,
               void *stream)
 {
+    const bool soa = P->opts.layout == MP_LAYOUT_SOA;
+    if (P->opts.coloring == MP_COLOR_GLOBAL || P->opts.coloring == MP_COLOR_ATOMIC) {
+        const float kh = (float)kappa;
+        const dw kap{kh, (float)(kappa - (double)kh)};
+        return soa ? hex_direct_dw_t<true>(P, x, v, sig, f, vol, kap, as_stream(stream))
+                   : hex_direct_dw_t<false>(P, x, v, sig, f, vol, kap, as_stream(stream));
+    }
     if (P->opts.coloring != MP_COLOR_HIER) return MP_EPLAN;
-    return P->opts.layout == MP_LAYOUT_SOA ? hex_dw_t<true>(P, x, v, sig, f, vol, kappa, as_stream(stream))
-                                           : hex_dw_t<false>(P, x, v, sig, f, vol, kappa, as_stream(stream));
+    return soa ? hex_dw_t<true>(P, x, v, sig, f, vol, kappa, as_stream(stream))
+               : hex_dw_t<false>(P, x, v, sig, f, vol, kappa, as_stream(stream));
 }

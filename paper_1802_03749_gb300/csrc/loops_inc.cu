@@ -1,13 +1,13 @@
 // Increment-only loops: indirect increments with (almost) no indirect reads.
 //
-//   space_disc  edges -> 2 cells (Sec. 3.1.3, the access pattern of Volna's
+//   space_disc  edges -> 2 cells (Sec. 3.1.2, the access pattern of Volna's
 //               SpaceDiscretization): per edge 7 values and 1 integer read
 //               directly, per cell 1 value read (the inverse area) and 4
 //               incremented.  With d = (F0, F1, F2, P, L, nx, ny):
 //                 w = L (F0, F1 + P nx, F2 + P ny, P)
 //                 res[c1] -= w / A[c1];  res[c2] += w / A[c2] unless the
 //                 edge is a boundary edge (flag 1, its cell listed twice).
-//   getacc      cells -> 4 nodes (Sec. 3.1.4, the access pattern of
+//   getacc      cells -> 4 nodes (Sec. 3.1.3, the access pattern of
 //               BookLeaf's getacc_scatter): per cell 17 values read directly,
 //               (rho, m[4], w[4], fx[4], fy[4]); node k of the cell gets
 //               (m_k, rho w_k, fx_k, fy_k).

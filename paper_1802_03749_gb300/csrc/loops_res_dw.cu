@@ -17,6 +17,9 @@
 //    to the FP64 res in FP64 at write-back.
 // Measured against the FP64 oracle the result agrees to ~1e-13 rel-L2.
 //
+// GLOBAL and ATOMIC plans run the baselines of Sec. 2.1 in the same
+// arithmetic (res_calc_direct_dw).
+//
 // GATHER form: instead of the thread-coloured increments each thread
 // stores its flux in shared memory, one barrier, and the thread that staged
 // a cell sums that cell's edge fluxes (the plan's block-local inverse map,
@@ -49,6 +52,64 @@ __device__ __forceinline__ dw ld(const float2 *a, int i)
     return {v.x, v.y};
 }
 __device__ __forceinline__ void st(float2 *a, int i, dw v) { a[i] = make_float2(v.hi, v.lo); }
+
+// Per-cell primitives of a conserved state in double-word arithmetic:
+// u, v, p = (gam - 1)(E - (ru u + rv v)/2), H = E + p.  Sloppy additions
+// throughout: the kinetic energy sums two non-negative terms, E - kin =
+// p/(gam-1) has condition number 1 + (gam-1) gam M^2 / 2 (1.05 at Mach 0.4),
+// E + p adds positives.
+__device__ __forceinline__ void dw_cell_prims(dw R, dw RU, dw RV, dw EE, dw gm1, dw &u, dw &v, dw &p, dw &H)
+{
+    const dw ri = dw_recip_fast(R);
+    u = dw_mul(RU, ri);
+    v = dw_mul(RV, ri);
+    const dw kin = dw_scale2(dw_add_fast(dw_mul(RU, u), dw_mul(RV, v)), 0.5f);
+    p = dw_mul(gm1, dw_add_fast(EE, dw_neg(kin)));
+    H = dw_add_fast(EE, p);
+}
+
+// Edge flux from the half normal (nxh, nyh) = n/2 and both cells' states,
+// primitives and eps adt / 2 (a1, a2); each component is one compensated
+// sum of products:
+//   V = u nx/2 + v ny/2,  mu = eps (adt1 + adt2) / 2,
+//   f0 = r1 V1 + r2 V2 + mu r1 - mu r2
+//   f1 = ru1 V1 + ru2 V2 + (p1 + p2) nx/2 + mu ru1 - mu ru2   (f2 likewise)
+//   f3 = H1 V1 + H2 V2 + mu E1 - mu E2
+__device__ __forceinline__ void dw_edge_flux(dw nxh, dw nyh, dw r1, dw ru1, dw rv1, dw E1, dw a1, dw u1, dw v1,
+                                             dw p1, dw H1, dw r2, dw ru2, dw rv2, dw E2, dw a2, dw u2, dw v2, dw p2,
+                                             dw H2, dw f[4])
+{
+    const dw pp = dw_add_fast(p1, p2);  // two positive pressures, no cancellation
+    dw_acc A = dw_dot_begin(u1, nxh);
+    dw_dot_add(A, v1, nyh);
+    const dw V1 = dw_dot_end(A);
+    A = dw_dot_begin(u2, nxh);
+    dw_dot_add(A, v2, nyh);
+    const dw V2 = dw_dot_end(A);
+    const dw mu = dw_add_fast(a1, a2);
+    A = dw_dot_begin(r1, V1);
+    dw_dot_add(A, r2, V2);
+    dw_dot_add(A, mu, r1);
+    dw_dot_add(A, mu, dw_neg(r2));
+    f[0] = dw_dot_end(A);
+    A = dw_dot_begin(ru1, V1);
+    dw_dot_add(A, ru2, V2);
+    dw_dot_add(A, pp, nxh);
+    dw_dot_add(A, mu, ru1);
+    dw_dot_add(A, mu, dw_neg(ru2));
+    f[1] = dw_dot_end(A);
+    A = dw_dot_begin(rv1, V1);
+    dw_dot_add(A, rv2, V2);
+    dw_dot_add(A, pp, nyh);
+    dw_dot_add(A, mu, rv1);
+    dw_dot_add(A, mu, dw_neg(rv2));
+    f[2] = dw_dot_end(A);
+    A = dw_dot_begin(H1, V1);
+    dw_dot_add(A, H2, V2);
+    dw_dot_add(A, mu, E1);
+    dw_dot_add(A, mu, dw_neg(E2));
+    f[3] = dw_dot_end(A);
+}
 
 template <bool SOA, bool GATHER>
 __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *__restrict__ desc, int block0,
@@ -132,13 +193,8 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         }
         dw R = dw_from_double_int(r), RU = dw_from_double_int(ru), RV = dw_from_double_int(rv),
            EE = dw_from_double_int(E);
-        // sloppy additions throughout: the kinetic energy sums two
-        // non-negative terms, E - kin = p/(gam-1) has condition number
-        // 1 + (gam-1) gam M^2 / 2 (1.05 at Mach 0.4), E + p adds positives
-        dw ri = dw_recip_fast(R);
-        dw u = dw_mul(RU, ri), v = dw_mul(RV, ri);
-        dw kin = dw_scale2(dw_add_fast(dw_mul(RU, u), dw_mul(RV, v)), 0.5f);
-        dw p = dw_mul(gm1, dw_add_fast(EE, dw_neg(kin)));
+        dw u, v, p, H;
+        dw_cell_prims(R, RU, RV, EE, gm1, u, v, p, H);
         st(s_r, 9 * i, R);
         st(s_ru, 9 * i, RU);
         st(s_rv, 9 * i, RV);
@@ -147,7 +203,7 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         st(s_u, 9 * i, u);
         st(s_v, 9 * i, v);
         st(s_p, 9 * i, p);
-        st(s_H, 9 * i, dw_add_fast(EE, p));
+        st(s_H, 9 * i, H);
         if (GATHER) {
             const ushort4 *row = gat + (int64_t)(d.fp_start[1] + i) * gw4;
             for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = row[h];
@@ -192,45 +248,10 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
         // n = (y_a - y_b, x_b - x_a), exact in FP64 for nearby nodes; halved
         const dw nxh = dw_scale2(dw_from_double_int(s_y[na] - s_y[nb]), 0.5f);
         const dw nyh = dw_scale2(dw_from_double_int(s_x[nb] - s_x[na]), 0.5f);
-        const dw r1 = ld(s_r, 9 * c1), r2 = ld(s_r, 9 * c2);
-        const dw ru1 = ld(s_ru, 9 * c1), ru2 = ld(s_ru, 9 * c2);
-        const dw rv1 = ld(s_rv, 9 * c1), rv2 = ld(s_rv, 9 * c2);
-        // p1 + p2: two positive pressures, no cancellation
-        const dw pp = dw_add_fast(ld(s_p, 9 * c1), ld(s_p, 9 * c2));
-        // each component is one compensated sum of products:
-        //   V = u nx/2 + v ny/2,  mu = eps (adt1 + adt2) / 2,
-        //   f0 = r1 V1 + r2 V2 + mu r1 - mu r2
-        //   f1 = ru1 V1 + ru2 V2 + (p1 + p2) nx/2 + mu ru1 - mu ru2   (f2 likewise)
-        //   f3 = H1 V1 + H2 V2 + mu E1 - mu E2
-        dw_acc A = dw_dot_begin(ld(s_u, 9 * c1), nxh);
-        dw_dot_add(A, ld(s_v, 9 * c1), nyh);
-        const dw V1 = dw_dot_end(A);
-        A = dw_dot_begin(ld(s_u, 9 * c2), nxh);
-        dw_dot_add(A, ld(s_v, 9 * c2), nyh);
-        const dw V2 = dw_dot_end(A);
-        const dw mu = dw_add_fast(ld(s_a, 9 * c1), ld(s_a, 9 * c2));
-        A = dw_dot_begin(r1, V1);
-        dw_dot_add(A, r2, V2);
-        dw_dot_add(A, mu, r1);
-        dw_dot_add(A, mu, dw_neg(r2));
-        f[0] = dw_dot_end(A);
-        A = dw_dot_begin(ru1, V1);
-        dw_dot_add(A, ru2, V2);
-        dw_dot_add(A, pp, nxh);
-        dw_dot_add(A, mu, ru1);
-        dw_dot_add(A, mu, dw_neg(ru2));
-        f[1] = dw_dot_end(A);
-        A = dw_dot_begin(rv1, V1);
-        dw_dot_add(A, rv2, V2);
-        dw_dot_add(A, pp, nyh);
-        dw_dot_add(A, mu, rv1);
-        dw_dot_add(A, mu, dw_neg(rv2));
-        f[2] = dw_dot_end(A);
-        A = dw_dot_begin(ld(s_H, 9 * c1), V1);
-        dw_dot_add(A, ld(s_H, 9 * c2), V2);
-        dw_dot_add(A, mu, ld(s_E, 9 * c1));
-        dw_dot_add(A, mu, dw_neg(ld(s_E, 9 * c2)));
-        f[3] = dw_dot_end(A);
+        dw_edge_flux(nxh, nyh, ld(s_r, 9 * c1), ld(s_ru, 9 * c1), ld(s_rv, 9 * c1), ld(s_E, 9 * c1),
+                     ld(s_a, 9 * c1), ld(s_u, 9 * c1), ld(s_v, 9 * c1), ld(s_p, 9 * c1), ld(s_H, 9 * c1),
+                     ld(s_r, 9 * c2), ld(s_ru, 9 * c2), ld(s_rv, 9 * c2), ld(s_E, 9 * c2), ld(s_a, 9 * c2),
+                     ld(s_u, 9 * c2), ld(s_v, 9 * c2), ld(s_p, 9 * c2), ld(s_H, 9 * c2), f);
     }
     if constexpr (GATHER) {
         __syncthreads();  // every flux is computed: the primitives are dead
@@ -298,10 +319,114 @@ __global__ void __launch_bounds__(512, 4) res_calc_hier_dw(const mp_block_desc *
     }
 }
 
+// The baselines of Sec. 2.1 in the same double-word arithmetic, so that the
+// strategies compare at equal arithmetic: one thread per edge of [e0, e1)
+// gathers its two nodes and two cells from global memory (FP64), forms the
+// primitives of both cells and the flux as the staged kernel does, and
+//   GLOBAL (edges of one colour share no cell): res[c] = res[c] + f in
+//          FP64 (two FP64 additions, as the staged write-back);
+//   ATOMIC: atomicAdd of the nearest double of f (hi + lo, one FP64
+//          addition) into res.
+template <bool SOA, bool ATOMIC>
+__global__ void __launch_bounds__(256) res_calc_direct_dw(int e0, int e1, const int32_t *__restrict__ e2n,
+                                                          const int32_t *__restrict__ e2c,
+                                                          const double *__restrict__ x, const double *__restrict__ q,
+                                                          const double *__restrict__ adt, double *__restrict__ res,
+                                                          int64_t nnode, int64_t ncell, dw gm1, dw half_eps)
+{
+    mp_pdl_trigger();
+    const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    const int2 nab = reinterpret_cast<const int2 *>(e2n)[e];
+    const int2 cc = reinterpret_cast<const int2 *>(e2c)[e];
+    double xa, ya, xb, yb;
+    if (SOA) {
+        xa = x[nab.x];
+        ya = x[nnode + nab.x];
+        xb = x[nab.y];
+        yb = x[nnode + nab.y];
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(x)[nab.x];
+        const double2 b = reinterpret_cast<const double2 *>(x)[nab.y];
+        xa = a.x;
+        ya = a.y;
+        xb = b.x;
+        yb = b.y;
+    }
+    dw c[2][5];  // rho, ru, rv, E, eps adt / 2 of both cells
+    const int cell[2] = {cc.x, cc.y};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int64_t g = cell[s];
+        double v[4];
+        if (SOA) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = q[k * ncell + g];
+        } else {
+            const double2 *q2 = reinterpret_cast<const double2 *>(q) + 2 * g;
+            const double2 a = q2[0], b = q2[1];
+            v[0] = a.x;
+            v[1] = a.y;
+            v[2] = b.x;
+            v[3] = b.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[s][k] = dw_from_double_int(v[k]);
+        c[s][4] = dw_mul(dw_from_double_int(adt[g]), half_eps);
+    }
+    dw u1, v1, p1, H1, u2, v2, p2, H2;
+    dw_cell_prims(c[0][0], c[0][1], c[0][2], c[0][3], gm1, u1, v1, p1, H1);
+    dw_cell_prims(c[1][0], c[1][1], c[1][2], c[1][3], gm1, u2, v2, p2, H2);
+    const dw nxh = dw_scale2(dw_from_double_int(ya - yb), 0.5f);
+    const dw nyh = dw_scale2(dw_from_double_int(xb - xa), 0.5f);
+    dw f[4];
+    dw_edge_flux(nxh, nyh, c[0][0], c[0][1], c[0][2], c[0][3], c[0][4], u1, v1, p1, H1, c[1][0], c[1][1], c[1][2],
+                 c[1][3], c[1][4], u2, v2, p2, H2, f);
+    if (!ATOMIC) mp_pdl_wait();  // res: read-add-written by the previous colour's launch
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t j1 = SOA ? k * ncell + cc.x : 4 * (int64_t)cc.x + k;
+        const int64_t j2 = SOA ? k * ncell + cc.y : 4 * (int64_t)cc.y + k;
+        if (ATOMIC) {
+            const double d = f32_to_f64_int(f[k].hi) + f32_to_f64_int(f[k].lo);
+            atomicAdd(res + j1, d);
+            atomicAdd(res + j2, -d);
+        } else {
+            res[j1] = f64_add_dw(res[j1], f[k]);
+            res[j2] = f64_add_dw(res[j2], dw_neg(f[k]));
+        }
+    }
+}
+
+template <bool SOA>
+int res_calc_direct_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt, void *res, dw gm1,
+                         dw half_eps, cudaStream_t s)
+{
+    const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;
+    auto kern = atomic ? res_calc_direct_dw<SOA, true> : res_calc_direct_dw<SOA, false>;
+    bool overlap = false;
+    for (int c = 0; c < P->ncolors; ++c) {
+        const int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
+        if (e1 <= e0) continue;
+        MP_CUDA_TRY(mp_launch(kern, (e1 - e0 + 255) / 256, 256, 0, s, overlap && !atomic, e0, e1, P->dev.map[0],
+                              P->dev.map[1], (const double *)x, (const double *)q, (const double *)adt,
+                              (double *)res, P->maps[0].to_size, P->maps[1].to_size, gm1, half_eps));
+        overlap = true;
+    }
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
 template <bool SOA>
 int res_calc_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt, void *res, double gam, double eps,
                   cudaStream_t s)
 {
+    // constants as the nearest double-words of their FP64 values
+    const double g1 = gam - 1.0, he = 0.5 * eps;
+    const float g1h = (float)g1, heh = (float)he;
+    const dw gm1{g1h, (float)(g1 - (double)g1h)}, half_eps{heh, (float)(he - (double)heh)};
+    if (P->opts.coloring == MP_COLOR_GLOBAL || P->opts.coloring == MP_COLOR_ATOMIC)
+        return res_calc_direct_dw_t<SOA>(P, x, q, adt, res, gm1, half_eps, s);
     if (P->opts.coloring != MP_COLOR_HIER || P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
     const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
     const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
@@ -315,10 +440,6 @@ int res_calc_dw_t(const mp_plan *P, const void *x, const void *q, const void *ad
     if (rc != MP_OK) return rc;
     int *err = nullptr;
     if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
-    // constants as the nearest double-words of their FP64 values
-    const double g1 = gam - 1.0, he = 0.5 * eps;
-    const float g1h = (float)g1, heh = (float)he;
-    const dw gm1{g1h, (float)(g1 - (double)g1h)}, half_eps{heh, (float)(he - (double)heh)};
     bool overlap = false;  // the first launch follows the caller's work: plain stream order
     for (int c = 0; c < P->ncolors; ++c) {
         int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;

@@ -1,5 +1,6 @@
-"""The multi-process logic of bench.py (replicas: slowest rank's time,
-whole-job rate) on two gloo ranks on the CPU."""
+"""The multi-process logic of bench.py (replicas: the slowest rank's time
+per repetition, the median repetition, the whole-job rate) on two gloo
+ranks on the CPU."""
 import os
 import socket
 
@@ -21,9 +22,11 @@ def _rank(rank, world, port, out):
 
     import bench
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    ms = bench.max_over_ranks(1.0 + rank, dist)       # rank 1 is the slower replica
+    # per-repetition times: rank 1 is slower in the first, rank 0 in the second
+    reps = bench.max_over_ranks([1.0 + rank, 3.0 - rank, 2.0], dist)
+    ms = float(sorted(reps)[1])                       # the median repetition
     rate = bench.job_rate(1000, world, ms)
-    out[rank] = (ms, rate)
+    out[rank] = (tuple(reps), ms, rate)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -40,10 +43,10 @@ def test_two_rank_aggregation():
     for p in procs:
         p.join(60)
         assert p.exitcode == 0
-    assert out[0] == out[1] == (2.0, pytest.approx(2 * 1000 / 2e-3))
+    assert out[0] == out[1] == ((2.0, 3.0, 2.0), 2.0, pytest.approx(2 * 1000 / 2e-3))
 
 
 def test_single_process_aggregation():
     import bench
-    assert bench.max_over_ranks(3.5, None) == 3.5
+    assert bench.max_over_ranks([3.5, 1.0], None) == [3.5, 1.0]
     assert bench.job_rate(10, 1, 5.0) == pytest.approx(2000.0)

@@ -113,3 +113,26 @@ def test_adjoint_full_size():
         qb, xb = gpu_adjoint(m, q, adt, rb, P, compute=compute)
         assert rel_l2(qb, qr) <= 1e-12
         assert rel_l2(xb, xr) <= 1e-12
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("compute", [None, "dw"])
+def test_adjoint_fd_full_size(compute):
+    """The adjoint workload (1200x600 quads, res_bar ~ N(0,1)): central
+    finite differences of the oracle's forward res_calc (h = 1e-6) on 100
+    random directions agree with the GPU adjoint, native FP64 and
+    double-word, to FD accuracy."""
+    m, q, adt, rb, P = setup(1200, 600, "hier", "partition", "aos", block_size=128)
+    qb, xb = gpu_adjoint(m, q, adt, rb, P, compute=compute)
+    h = 1e-6
+    worst = 0.0
+    for d in meshgen.directions(m.ncell * 4 + m.nnode * 2, 100, seed=43):
+        dq = d[:4 * m.ncell].reshape(-1, 4) * q.std(axis=0)
+        dx = d[4 * m.ncell:].reshape(-1, 2) * m.h * 0.1
+        ad = float((qb * dq).sum() + (xb * dx).sum())
+        rp = oracle.res_calc(m.edge2node, m.edge2cell, m.x + h * dx, q + h * dq, adt)
+        rm = oracle.res_calc(m.edge2node, m.edge2cell, m.x - h * dx, q - h * dq, adt)
+        fd = float((rb * (rp - rm)).sum()) / (2 * h)
+        scale = float(np.abs(qb * dq).sum() + np.abs(xb * dx).sum())
+        worst = max(worst, abs(fd - ad) / scale)
+    assert worst <= 1e-7

@@ -83,10 +83,10 @@ def test_hex_thread_coloured_variant(dtype, staged):
         assert rel_l2(f, fr) <= 1e-5
 
 
-def run_hex_dw(m, sig, v, reorder, layout, block_size=128, staged=None):
+def run_hex_dw(m, sig, v, reorder, layout, block_size=128, staged=None, coloring="hier"):
     import paper_1802_03749_gb300 as ml
     from paper_1802_03749_gb300.mesh import HexPlan
-    H = HexPlan(m.nnode, m.elem2node, block_size=block_size, reorder=reorder, coloring="hier", layout=layout,
+    H = HexPlan(m.nnode, m.elem2node, block_size=block_size, reorder=reorder, coloring=coloring, layout=layout,
                 staged=staged)
     x = torch.tensor(H.to_plan(m.x, "node"), device="cuda")
     vd = torch.tensor(H.to_plan(v, "node"), device="cuda")
@@ -112,6 +112,19 @@ def test_hex_double_word_parity(reorder, layout):
         assert rel_l2(f, fr) <= 1e-12
 
 
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("reorder", ["none", "rcm"])
+@pytest.mark.parametrize("coloring", ["global", "atomic"])
+def test_hex_double_word_baselines(coloring, reorder, layout):
+    """Global colouring and atomics (Sec. 2.1) in double-word arithmetic on
+    FP64 data (a ragged last launch: 13^3 elements): within the FP64 bar."""
+    m, sig, v = case(13)
+    fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
+    f, vol = run_hex_dw(m, sig, v, reorder, layout, coloring=coloring)
+    assert rel_l2(vol, vr) <= 1e-12
+    assert rel_l2(f, fr) <= 1e-12
+
+
 @pytest.mark.parametrize("block_size", [32, 96, 256])
 def test_hex_double_word_gather_ragged_and_deterministic(block_size):
     m, sig, v = case(11)
@@ -122,12 +135,13 @@ def test_hex_double_word_gather_ragged_and_deterministic(block_size):
 
 
 @pytest.mark.slow
-def test_hex_double_word_full_size():
-    """The benchmark's hex workload, 120^3 elements: the oracle computes
-    every node."""
+@pytest.mark.parametrize("coloring", ["hier", "atomic"])
+def test_hex_double_word_full_size(coloring):
+    """The benchmark's hex workload, 120^3 elements, two-layer (partition)
+    and atomics (RCM): the oracle computes every node."""
     m = meshgen.hex_mesh(120)
     sig, v = meshgen.hex_fields(m)
-    f, vol = run_hex_dw(m, sig, v, "partition", "aos")
+    f, vol = run_hex_dw(m, sig, v, "partition" if coloring == "hier" else "rcm", "aos", coloring=coloring)
     fr, vr = oracle.hex_force(m.elem2node, m.x, v, sig)
     assert rel_l2(vol, vr) <= 1e-12
     assert rel_l2(f, fr) <= 1e-12

@@ -97,10 +97,10 @@ def test_res_calc_tiny_and_empty(ml):
     assert P.stats()["nblocks"] == 0
 
 
-def run_dw(ml, m, q, adt, reorder, layout, block_size=480, res0=None, staged=None):
+def run_dw(ml, m, q, adt, reorder, layout, block_size=480, res0=None, staged=None, coloring="hier"):
     from paper_1802_03749_gb300.mesh import AirfoilPlans
     P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                     block_size=block_size, reorder=reorder, coloring="hier", layout=layout, staged=staged)
+                     block_size=block_size, reorder=reorder, coloring=coloring, layout=layout, staged=staged)
     x = torch.tensor(P.to_plan(m.x, "node"), device="cuda")
     qd = torch.tensor(P.to_plan(q, "cell"), device="cuda")
     ad = torch.tensor(P.to_plan(adt, "cell"), device="cuda")
@@ -123,20 +123,63 @@ def test_res_calc_double_word_parity(ml, reorder, layout, staged):
     assert rel_l2(got - r0, ref - r0) <= 1e-12
 
 
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("reorder", ["none", "rcm"])
+@pytest.mark.parametrize("coloring", ["global", "atomic"])
+def test_res_calc_double_word_baselines(ml, coloring, reorder, layout):
+    """Global colouring and atomics (Sec. 2.1) in double-word arithmetic on
+    FP64 data: within the FP64 bar, like the two-layer form."""
+    m, q, adt = case(200, 100)
+    r0 = 0.01 * np.cos(np.arange(q.size)).reshape(q.shape)
+    got = run_dw(ml, m, q, adt, reorder, layout, res0=r0, coloring=coloring)
+    ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt, res=r0.copy())
+    assert rel_l2(got - r0, ref - r0) <= 1e-12
+
+
+@pytest.mark.parametrize("xs,qs", [(1e-12, 1.0), (1e12, 1.0), (1.0, 1e15), (1.0, 1e-15), (1e-6, 1e-10),
+                                   (1e6, 1e10)])
+def test_res_calc_double_word_scaled_inputs(ml, xs, qs):
+    """The double-word arithmetic (FP32 exponent range) on inputs scaled far
+    from the unit free stream: coordinates by xs, states by qs (adt follows
+    from them): every form stays within the FP64 bar."""
+    m0, q0, _ = case(60, 30)
+    import copy
+    m = copy.copy(m0)
+    m.x = m0.x * xs
+    q = q0 * qs
+    adt = oracle.adt_calc(m.cell2node, m.x, q)
+    ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
+    for coloring, staged in (("hier", None), ("hier", "simple"), ("global", None), ("atomic", None)):
+        got = run_dw(ml, m, q, adt, "partition" if coloring == "hier" else "rcm", "aos", block_size=256,
+                     staged=staged, coloring=coloring)
+        assert rel_l2(got, ref) <= 1e-12, (coloring, staged)
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("compute", [None, "dw", "dw_colour"])
+@pytest.mark.parametrize("compute", ["f64", "f64_480", "dw", "dw_colour", "dw_global", "dw_atomic", "f32"])
 def test_res_calc_full_size_parity(ml, compute):
     """The benchmark's workload: 2400x1200 quads, two-layer colouring,
-    RCM + partition, AoS, FP64 data (double-word arithmetic at block 256,
-    the benchmark's launch, or native FP64 at 480); the oracle computes
-    every cell."""
+    RCM + partition, AoS at block 256 (the benchmark's launch): native FP64
+    with thread-coloured increments (the headline), double-word arithmetic
+    (gather and thread colours) and FP32 (gather); native FP64 at block 480;
+    the double-word global-colour and atomic baselines on the RCM order.
+    The oracle computes every cell."""
     m, q, adt = case(2400, 1200)
     if compute == "dw":
         got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256)
     elif compute == "dw_colour":
         got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256, staged="simple")
+    elif compute in ("dw_global", "dw_atomic"):
+        got = run_dw(ml, m, q, adt, "rcm", "aos", coloring=compute[3:])
+    elif compute == "f32":
+        got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f32", block_size=256, staged="gather")
+        ref = oracle.res_calc(m.edge2node, m.edge2cell, round_to(m.x, np.float32), round_to(q, np.float32),
+                              round_to(adt, np.float32))
+        assert rel_l2(got, ref) <= 1e-5
+        return
     else:
-        got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64")
+        got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64",
+                              block_size=256 if compute == "f64" else 480, staged="simple")
     ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
     assert rel_l2(got, ref) <= 1e-12
 

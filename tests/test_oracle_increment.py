@@ -1,5 +1,5 @@
 """Pins of the oracle's increment-only loops (Volna-style edge loop,
-Sec. 3.1.3; BookLeaf-style cell loop, Sec. 3.1.4) against closed forms,
+Sec. 3.1.2; BookLeaf-style cell loop, Sec. 3.1.3) against closed forms,
 conservation and cell- or node-centric brute force.  CPU only."""
 import numpy as np
 import pytest
