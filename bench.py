@@ -145,7 +145,7 @@ def record_traffic(args):
 
 def default_staged(compute):
     """The library's default increment form of the headline kernel."""
-    return "simple" if compute == "f64" else "gather"
+    return "gather"
 
 
 def useful_bytes_res_calc(ncell, nnode, nedge, elt):
@@ -803,6 +803,8 @@ def main():
                     help="f64: FP64 data and arithmetic (the paper's); dw: FP64 data with double-word "
                          "arithmetic; f32: FP32 data")
     ap.add_argument("--no-variants", action="store_true", help="skip the baseline variants")
+    ap.add_argument("--variants", default=None,
+                    help="comma list of the variants to measure (default: all; e.g. atomic_rcm_f32_soa)")
     ap.add_argument("--rows", default="hex,adjoint,batch,shapes,increment,face,precision",
                     help="other loops to measure (comma list of hex, adjoint, batch, shapes, increment, face, "
                          "precision; none for none)")
@@ -986,8 +988,11 @@ def main():
         "reuse": st["reuse_all"], "plan_seconds": st["seconds_total"], "parity": head_parity}}
     if not args.no_variants:
         plans = {("hier", "partition", args.layout, False): P}
+        pick = set(args.variants.split(",")) if args.variants else None
         for key, name, comp_v, staged in res_variants(compute):
             if name == head_name and key == ("hier", "partition", args.layout, False):
+                continue
+            if pick is not None and name not in pick:
                 continue
             try:
                 if key not in plans:

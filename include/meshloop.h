@@ -121,10 +121,10 @@ typedef struct {
     int32_t staged;      /* MP_STAGED_* implementation of HIER loops; -1: the loop's
                             default (hex assembly, whose 3D blocks need ~10 thread
                             colours: MP_STAGED_SMEM_ATOMIC in FP32, MP_STAGED_WARP_AGG
-                            in FP64; MP_STAGED_GATHER for FP32
-                            and double-word res_calc, the double-word hex assembly
-                            and adjoint, and the increment-only loops;
-                            MP_STAGED_SIMPLE otherwise)                               */
+                            in FP64; MP_STAGED_GATHER for res_calc in every
+                            arithmetic, the double-word hex assembly and adjoint,
+                            and the increment-only loops; MP_STAGED_SIMPLE
+                            otherwise)                                               */
     int32_t recolor;     /* HIER: after the first-fit block colouring, empty the last
                             colours when they hold few blocks (at most 1/32 of them)
                             by moving each of their blocks to an earlier colour
@@ -328,7 +328,9 @@ enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2,
  * increments in shared memory, one barrier, then every footprint point sums
  * the increments of its iterations in the block (block-local inverse map,
  * fixed order: deterministic) and writes back once.  res_calc (native and
- * double-word).                                                          */
+ * double-word; native FP32 blocks of more than 256 edges, a multiple of
+ * 64, run two edges per thread), hex assembly and the adjoint (double-
+ * word), the increment-only loops and the face flux.                      */
 
 /* Far-field boundary flux bres_calc over boundary edges: with
  * q_b = (q_c + qinf)/2,  res[c] += F(q_b).n + eps adt_c (q_c - qinf).

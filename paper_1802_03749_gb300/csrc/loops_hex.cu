@@ -110,11 +110,53 @@ __device__ __forceinline__ void load3(const T *__restrict__ p, int64_t n, int64_
     }
 }
 
-// smem per footprint node: x[3], v[3], f (prefetched, incremented)[3] and the global id
+// smem per footprint node: one record of 8 values (x[3], v[0] | v[1], v[2],
+// two unused), read with two vector loads per corner; f (prefetched,
+// incremented)[3] and the global id
 template <typename T>
 __host__ __device__ constexpr int hex_smem_per_node()
 {
-    return 9 * (int)sizeof(T) + 4;
+    return 11 * (int)sizeof(T) + 4;
+}
+
+// A node record of 8 values in shared memory (16-byte aligned): x, y, z,
+// vx | vy, vz, -, -.
+template <typename T>
+__device__ __forceinline__ void st_node_rec(T *rec, int i, const T xv[6])
+{
+    if (sizeof(T) == 8) {
+        double2 *p = reinterpret_cast<double2 *>(rec) + 4 * i;
+        p[0] = make_double2((double)xv[0], (double)xv[1]);
+        p[1] = make_double2((double)xv[2], (double)xv[3]);
+        p[2] = make_double2((double)xv[4], (double)xv[5]);
+    } else {
+        float4 *p = reinterpret_cast<float4 *>(rec) + 2 * i;
+        p[0] = make_float4((float)xv[0], (float)xv[1], (float)xv[2], (float)xv[3]);
+        p[1] = make_float4((float)xv[4], (float)xv[5], 0.f, 0.f);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void ld_node_rec(const T *rec, int i, T xe[3], T ve[3])
+{
+    if (sizeof(T) == 8) {
+        const double2 *p = reinterpret_cast<const double2 *>(rec) + 4 * i;
+        const double2 a = p[0], b = p[1], c = p[2];
+        xe[0] = (T)a.x;
+        xe[1] = (T)a.y;
+        xe[2] = (T)b.x;
+        ve[0] = (T)b.y;
+        ve[1] = (T)c.x;
+        ve[2] = (T)c.y;
+    } else {
+        const float4 *p = reinterpret_cast<const float4 *>(rec) + 2 * i;
+        const float4 a = p[0], b = p[1];
+        xe[0] = (T)a.x;
+        xe[1] = (T)a.y;
+        xe[2] = (T)a.z;
+        ve[0] = (T)a.w;
+        ve[1] = (T)b.x;
+        ve[2] = (T)b.y;
+    }
 }
 
 // increments: 0 thread colours, 1 shared-memory atomics, 3 warp-aggregated
@@ -128,9 +170,8 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
                                                 int64_t nelem, int cap, T kappa, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s_x = reinterpret_cast<T *>(smem_raw);  // [3][cap]
-    T *s_v = s_x + 3 * cap;                    // [3][cap]
-    T *s_f = s_v + 3 * cap;                    // [3][cap]
+    T *s_xv = reinterpret_cast<T *>(smem_raw);  // [cap][8] node records
+    T *s_f = s_xv + 8 * cap;                    // [3][cap]
     int *s_gid = reinterpret_cast<int *>(s_f + 3 * cap);
 
     mp_pdl_trigger();
@@ -164,23 +205,23 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         const int i1 = i0 + (int)blockDim.x;
         const bool two = i1 < nn;
         const int g0 = fpn[i0], g1 = two ? fpn[i1] : g0;
-        T x0[3], x1[3], v0[3], v1[3];
-        load3<T, SOA>(x, nnode, g0, x0[0], x0[1], x0[2]);
-        load3<T, SOA>(v, nnode, g0, v0[0], v0[1], v0[2]);
-        load3<T, SOA>(x, nnode, g1, x1[0], x1[1], x1[2]);
-        load3<T, SOA>(v, nnode, g1, v1[0], v1[1], v1[2]);
-        stage3(s_x, i0, x0[0], x0[1], x0[2]);
-        stage3(s_v, i0, v0[0], v0[1], v0[2]);
+        T xv0[6], xv1[6];
+        load3<T, SOA>(x, nnode, g0, xv0[0], xv0[1], xv0[2]);
+        load3<T, SOA>(v, nnode, g0, xv0[3], xv0[4], xv0[5]);
+        if (two) {
+            load3<T, SOA>(x, nnode, g1, xv1[0], xv1[1], xv1[2]);
+            load3<T, SOA>(v, nnode, g1, xv1[3], xv1[4], xv1[5]);
+        }
+        st_node_rec(s_xv, i0, xv0);
         s_gid[i0] = g0;
         if (two) {
-            stage3(s_x, i1, x1[0], x1[1], x1[2]);
-            stage3(s_v, i1, v1[0], v1[1], v1[2]);
+            st_node_rec(s_xv, i1, xv1);
             s_gid[i1] = g1;
         }
         mp_pdl_wait();  // f: written by the previous colour's launch
         T f0[3], f1[3];
         load3<T, SOA>(f, nnode, g0, f0[0], f0[1], f0[2]);
-        load3<T, SOA>(f, nnode, g1, f1[0], f1[1], f1[2]);
+        if (two) load3<T, SOA>(f, nnode, g1, f1[0], f1[1], f1[2]);
         stage3(s_f, i0, f0[0], f0[1], f0[2]);
         if (two) stage3(s_f, i1, f1[0], f1[1], f1[2]);
     }
@@ -199,12 +240,7 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
         loc[7] = l.w >> 16;
         T xe[8][3], ve[8][3];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                xe[i][a] = s_x[a * cap + loc[i]];
-                ve[i][a] = s_v[a * cap + loc[i]];
-            }
+        for (int i = 0; i < 8; ++i) ld_node_rec(s_xv, loc[i], xe[i], ve[i]);
         T s0, s1, s2, V;
         load3<T, SOA>(sig, nelem, e, s0, s1, s2);
         hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
