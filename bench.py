@@ -65,7 +65,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM traffic records: one text file per configuration under profiles/,
 # written by --record-traffic from an ncu CSV of the headline kernel
 TRAFFIC_SOURCES = ("loops_res.cu", "loops_res_dw.cu", "dw.cuh", "common.cuh", "plan_internal.h", "plan.cpp")
-HEAD_KERNEL = {"f64": "res_calc_hier", "f32": "res_calc_hier", "dw": "res_calc_hier_dw"}
+HEAD_KERNEL = {"f64": "res_calc_hier_g", "f32": "res_calc_hier_g", "dw": "res_calc_hier_dw"}
 
 
 def sources_sha256():
