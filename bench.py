@@ -713,6 +713,11 @@ def bench_batch(ml, torch, timer, args):
     B.capture(steps_per_graph=1)
     ms_graph, _ = timer(lambda: B.graph.replay(), 20, 3)
     ms_batch_eager, _ = timer(B.step, 20, 3)
+    # the fused res_calc as one persistent launch for all colour phases
+    Bp = AirfoilBatch(meshes, states, qinf, choices, dtype="f32", res_staged="persistent")
+    Bp.capture(steps_per_graph=1)
+    ms_graph_persistent, _ = timer(lambda: Bp.graph.replay(), 20, 3)
+    del Bp
     # the same meshes with the same plans (the autotuner's choice per mesh),
     # one step per mesh: eagerly (64 launch sequences) and as 64 graphs
     per = [AirfoilStep(AirfoilPlans(mm.ncell, mm.nnode, mm.edge2node, mm.edge2cell, mm.bedge2node, mm.bedge2cell,
@@ -738,7 +743,8 @@ def bench_batch(ml, torch, timer, args):
     rows["batch_step_f32"] = {
         "workload": f"{args.batch} quad meshes, {cells} cells, {edges} edges, full time step, FP32 data, "
                     "FP64 update and residual sum",
-        "ms_graph_batched": ms_graph, "ms_eager_batched": ms_batch_eager, "ms_per_mesh_launches": ms_per,
+        "ms_graph_batched": ms_graph, "ms_graph_batched_persistent_res_calc": ms_graph_persistent,
+        "ms_eager_batched": ms_batch_eager, "ms_per_mesh_launches": ms_per,
         "ms_per_mesh_graphs": ms_per_graphs, "speedup_vs_per_mesh": ms_per / ms_graph,
         "speedup_vs_per_mesh_graphs": ms_per_graphs / ms_graph, "gedges_s": edges / ms_graph / 1e6,
         "autotune": tuned, "autotune_seconds": tune_s}
@@ -762,6 +768,7 @@ def res_variants(compute_head):
         (part, "two_layer_partition_f64_smem_atomic", "f64", "smem_atomic"),
         (part, "two_layer_partition_f64_warp_agg", "f64", "warp_agg"),
         (part, "two_layer_partition_f64_pipelined", "f64", "pipelined"),
+        (part, "two_layer_partition_f64_persistent", "f64", "persistent"),
         (part_ff, "two_layer_partition_f64_first_fit_colours", "f64", "simple"),
         (rcm, "two_layer_rcm_f64", "f64", None),
         (g_rcm, "global_rcm_f64", "f64", None), (g_none, "global_none_f64", "f64", None),
@@ -779,6 +786,7 @@ def res_variants(compute_head):
         (part, "two_layer_partition_f32_simple", "f32", "simple"),
         (part, "two_layer_partition_f32_smem_atomic", "f32", "smem_atomic"),
         (part, "two_layer_partition_f32_pipelined", "f32", "pipelined"),
+        (part, "two_layer_partition_f32_persistent", "f32", "persistent"),
         (rcm, "two_layer_rcm_f32", "f32", None),
         (part_soa, "two_layer_partition_f32_gather_soa", "f32", "gather"),
         (g_rcm, "global_rcm_f32", "f32", None), (g_rcm_soa, "global_rcm_f32_soa", "f32", None),
@@ -797,7 +805,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--layout", default="aos", choices=["aos", "soa"])
-    ap.add_argument("--staged", default=None, choices=["simple", "gather", "smem_atomic", "pipelined", "warp_agg"],
+    ap.add_argument("--staged", default=None,
+                    choices=["simple", "gather", "smem_atomic", "pipelined", "warp_agg", "persistent"],
                     help="increment form of the staged headline kernel (default: the library's)")
     ap.add_argument("--compute", default="f64", choices=["f64", "dw", "f32"],
                     help="f64: FP64 data and arithmetic (the paper's); dw: FP64 data with double-word "

@@ -313,7 +313,19 @@ int loop_res_calc_host(const mp_plan *plan, int32_t dtype, const void *x, const 
  *    double-word res_calc or the adjoint, which run SIMPLE.
  * Block colouring orders the write-back in every variant.                */
 enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2, MP_STAGED_GATHER = 3,
-       MP_STAGED_INC_ONLY = 4, MP_STAGED_INC_ONLY_GATHER = 5, MP_STAGED_WARP_AGG = 6 };
+       MP_STAGED_INC_ONLY = 4, MP_STAGED_INC_ONLY_GATHER = 5, MP_STAGED_WARP_AGG = 6,
+       MP_STAGED_PERSISTENT = 7 };
+/* MP_STAGED_PERSISTENT: res_calc (native FP64 and FP32, gather increments)
+ * in ONE cooperative launch per call instead of one launch per block
+ * colour: a grid of resident CTAs walks the block-descriptor table colour
+ * by colour (each CTA takes the colour's next block from a counter), and
+ * the CTAs meet at a grid-wide barrier between colours.  The barrier's wait is bounded (1
+ * s): if it runs out the CTAs return, the result is invalid and
+ * mp_check_device_status reports MP_ETIMEOUT; nothing hangs.  The barrier
+ * and block counters belong to the plan: calls on one plan must not
+ * overlap.  On a
+ * fused batch plan (mesh_batch_build) this runs every mesh of the batch in
+ * one launch.  Other dtypes run MP_STAGED_GATHER.                        */
 /* MP_STAGED_WARP_AGG: warp-aggregated increments: lanes of a warp that
  * increment the same point combine their values with a segmented shuffle
  * tree (match.any groups) and one lane adds the sum with a shared-memory
@@ -476,6 +488,16 @@ const char *mp_error_string(int code);
  * launch provides, and returned without touching memory) or MP_ETIMEOUT (a
  * bounded device-side wait gave up).  Synchronises the stream.          */
 int mp_check_device_status(void *stream);
+/* Diagnostic of the bounded grid-wide wait that the persistent launches
+ * (MP_STAGED_PERSISTENT) use between block colours; not in the paper.
+ * Launches nctas resident CTAs (1 <= nctas <= the SM count, cooperative
+ * launch) on `stream`; each arrives once and waits for nctas + missing
+ * arrivals, at most wait_ns nanoseconds (0..1e9).  missing = 0: the wait
+ * completes; missing > 0: it can only run out, every CTA records
+ * MP_ETIMEOUT in the device error word and returns (the GPU and the
+ * context stay usable), which mp_check_device_status then reports.
+ * Errors: MP_EINVAL (sizes), MP_ECUDA.                                  */
+int mp_grid_wait_test(int32_t nctas, int64_t wait_ns, int32_t missing, void *stream);
 /* Library version string. */
 const char *mp_version(void);
 

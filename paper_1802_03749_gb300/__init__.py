@@ -25,6 +25,7 @@ __all__ = [
     "MeshLoopError", "Plan", "lib", "loop_res_calc", "loop_bres_calc", "loop_adt_calc", "loop_save_soln",
     "loop_res_calc_host", "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint",
     "loop_space_disc", "loop_getacc", "loop_face_flux", "mesh_map_renumber", "mp_check_device_status",
+    "mp_grid_wait_test",
     "REORDER", "COLORING", "LAYOUT", "MP_MAX_BLOCK_COLORS",
 ]
 
@@ -37,7 +38,7 @@ MP_MAX_MAPS = 4
 MP_MAX_TOSETS = 2
 REORDER = {"none": 0, "rcm": 1, "partition": 2}
 STAGED = {None: -1, "pipelined": 0, "simple": 1, "smem_atomic": 2, "gather": 3, "inc_only": 4,
-          "inc_only_gather": 5, "warp_agg": 6}
+          "inc_only_gather": 5, "warp_agg": 6, "persistent": 7}
 COLORING = {"hier": 0, "global": 1, "atomic": 2, "twostep": 3}
 LAYOUT = {"aos": 0, "soa": 1}
 DTYPE = {"f64": 0, "f32": 1, "f64dw": 2}
@@ -114,6 +115,7 @@ SIGNATURES = {
     "loop_face_flux": (_I32, [_P, _I32, _P, _P, _P, _D, _D, _D, _P]),
     "mp_error_string": (ctypes.c_char_p, [_I32]),
     "mp_check_device_status": (_I32, [_P]),
+    "mp_grid_wait_test": (_I32, [_I32, _I64, _I32, _P]),
     "mp_version": (ctypes.c_char_p, []),
 }
 
@@ -434,3 +436,8 @@ def loop_face_flux(plan: Plan, fdata, cdata, res, gam: float = 1.4, mu: float = 
 
 def mp_check_device_status(stream=None):
     _check(lib().mp_check_device_status(_stream(stream)), "mp_check_device_status")
+
+
+def mp_grid_wait_test(nctas: int, wait_ns: int, missing: int = 0, stream=None):
+    """Diagnostic of the bounded grid-wide wait (``mp_grid_wait_test``)."""
+    _check(lib().mp_grid_wait_test(int(nctas), int(wait_ns), int(missing), _stream(stream)), "mp_grid_wait_test")

@@ -104,6 +104,54 @@ __device__ __forceinline__ unsigned dynamic_smem_bytes()
 // Device error word codes (read by mp_check_device_status).
 enum { MP_DEVERR_NONE = 0, MP_DEVERR_TIMEOUT = 1, MP_DEVERR_SMEM = 2 };
 
+// Limit of a device-side wait (ns of %globaltimer) in the library's
+// persistent kernels: a wait that runs out records MP_DEVERR_TIMEOUT and
+// the kernel returns instead of waiting on.
+constexpr unsigned long long MP_GRID_WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long mp_globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned mp_ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident) with a
+// bounded wait: each CTA's thread 0 publishes the CTA's writes (fence) and
+// arrives on a counter that the launch starts at 0, then waits until
+// `target` arrivals are visible (acquire) or wait_ns has passed.  Returns
+// false when the wait gave up: MP_DEVERR_TIMEOUT is then in the error word
+// and the caller must return (its results are invalid).  Uniform per CTA.
+__device__ __forceinline__ bool mp_grid_barrier(unsigned *count, unsigned target, unsigned long long wait_ns,
+                                                int *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        const unsigned long long t0 = mp_globaltimer_ns();
+        int ok = 1;
+        while (mp_ld_acquire(count) < target) {
+            if (mp_globaltimer_ns() - t0 > wait_ns) {
+                atomicExch(err, MP_DEVERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(256);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // Library-owned device error word of the current device.
 int mp_device_error_word(int **word);
 

@@ -33,6 +33,8 @@ void mp_plan_free_device(mp_plan *P)
     cudaFree(d.fp);
     cudaFree(d.tcolor);
     cudaFree(d.gat);
+    cudaFree(d.color_off);
+    cudaFree(d.bar);
     for (auto &m : d.map) cudaFree(m);
     cudaFree(d.inv_off);
     cudaFree(d.inv_idx);
@@ -71,6 +73,13 @@ int mp_plan_ensure_device(const mp_plan *cplan)
         if (!P->gat_tab.empty() &&
             (rc = upload(&d.gat, P->gat_tab.data(), P->gat_tab.size(), bytes)) != MP_OK)
             goto fail;
+        if ((rc = upload(&d.color_off, P->color_offsets.data(), P->color_offsets.size(), bytes)) != MP_OK)
+            goto fail;
+        {
+            // grid-barrier arrivals and one block counter per colour
+            const std::vector<unsigned> zeros((size_t)P->ncolors + 1, 0u);
+            if ((rc = upload(&d.bar, zeros.data(), zeros.size(), bytes)) != MP_OK) goto fail;
+        }
     } else {
         for (int m = 0; m < P->nmaps; ++m)
             if ((rc = upload(&d.map[m], P->maps[m].idx.data(), P->maps[m].idx.size(), bytes)) != MP_OK) goto fail;
@@ -142,6 +151,49 @@ extern "C" int mp_check_device_status(void *stream)
         MP_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
         return h == MP_DEVERR_SMEM ? MP_ESMEM : MP_ETIMEOUT;
     }
+    return MP_OK;
+}
+
+// ------------------------------------------------- bounded grid-wide wait
+
+namespace {
+unsigned *g_wait_count[64] = {nullptr};
+
+// Every CTA arrives once on the counter and waits for `target` arrivals:
+// with target above the grid size the wait can only run out.
+__global__ void grid_wait_probe(unsigned *count, unsigned target, unsigned long long wait_ns, int *err)
+{
+    mp_grid_barrier(count, target, wait_ns, err);
+}
+}  // namespace
+
+extern "C" int mp_grid_wait_test(int32_t nctas, int64_t wait_ns, int32_t missing, void *stream)
+{
+    if (nctas < 1 || missing < 0 || wait_ns < 0 || wait_ns > (int64_t)MP_GRID_WAIT_NS) return MP_EINVAL;
+    int dev = 0, sms = 0;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    MP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 0 || dev >= 64 || nctas > sms) return MP_EINVAL;  // one CTA per SM at most: all resident
+    int *err = nullptr;
+    int rc = mp_device_error_word(&err);
+    if (rc != MP_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_wait_count[dev]) MP_CUDA_TRY(cudaMalloc(&g_wait_count[dev], sizeof(unsigned)));
+    }
+    cudaStream_t s = as_stream(stream);
+    MP_CUDA_TRY(cudaMemsetAsync(g_wait_count[dev], 0, sizeof(unsigned), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nctas);
+    cfg.blockDim = dim3(32);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, grid_wait_probe, g_wait_count[dev], (unsigned)(nctas + missing),
+                                   (unsigned long long)wait_ns, err));
     return MP_OK;
 }
 

@@ -46,23 +46,26 @@ __host__ __device__ constexpr int res_smem_per_node()
 constexpr int kIncColor = 0, kIncAtomic = 1, kIncShuffle = 3;
 
 
-template <typename T, bool SOA>
+// CG: read through L2 only (ld.global.cg), for values another CTA of the
+// same launch wrote (this SM's L1 may hold an older copy)
+template <typename T, bool SOA, bool CG = false>
 __device__ __forceinline__ void load_res(const T *__restrict__ res, int64_t ncell, int g, T &r0, T &r1, T &r2, T &r3)
 {
     if (SOA) {
-        r0 = res[g];
-        r1 = res[ncell + g];
-        r2 = res[2 * ncell + g];
-        r3 = res[3 * ncell + g];
+        r0 = CG ? __ldcg(res + g) : res[g];
+        r1 = CG ? __ldcg(res + ncell + g) : res[ncell + g];
+        r2 = CG ? __ldcg(res + 2 * ncell + g) : res[2 * ncell + g];
+        r3 = CG ? __ldcg(res + 3 * ncell + g) : res[3 * ncell + g];
     } else if (sizeof(T) == 8) {
         const double2 *p = reinterpret_cast<const double2 *>(res) + 2 * (int64_t)g;
-        double2 a = p[0], b = p[1];
+        double2 a = CG ? __ldcg(p) : p[0], b = CG ? __ldcg(p + 1) : p[1];
         r0 = (T)a.x;
         r1 = (T)a.y;
         r2 = (T)b.x;
         r3 = (T)b.y;
     } else {
-        float4 a = reinterpret_cast<const float4 *>(res)[g];
+        const float4 *p = reinterpret_cast<const float4 *>(res) + g;
+        float4 a = CG ? __ldcg(p) : p[0];
         r0 = (T)a.x;
         r1 = (T)a.y;
         r2 = (T)a.z;
@@ -340,64 +343,111 @@ __device__ __forceinline__ void ld_row4(const T *base, int i, T &a, T &b, T &c, 
     }
 }
 
+// -v by flipping the sign bit: an integer operation, so FP64 negations
+// do not occupy the FP64 pipe
+__device__ __forceinline__ float flip_sign(float v) { return __int_as_float(__float_as_int(v) ^ (int)0x80000000); }
+__device__ __forceinline__ double flip_sign(double v)
+{
+    return __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v));
+}
+
 // The gather form of the staged kernel, with every value another thread
 // reads stored as one vector record in shared memory:
 //   T  cq[cap_c][4]   rho, ru, rv, E
 //   T  cp[cap_c][4]   u, v, p, H              (per-cell primitives)
 //   T  cr[cap_c][4]   res, prefetched at staging
-//   T  f[S][4]        one flux per edge of the block (S = cap_f, a multiple
-//                     of blockDim: each thread computes S / blockDim <= 2)
+//   T  f[2 S + 1][4]  FP32: the flux of every edge of the block (S =
+//                     blockDim) at [e], its negation at [S + e], zeros at
+//                     [2 S];  FP64: [S + 1][4], the fluxes (and a zero row)
 //   T  xh[cap_n][2]   half coordinates of the nodes
-//   ushort4 ge[gw4][cap_c]  gather rows of the cells
+//   ushort4 ge[gw4][cap_c]  the cells' gather rows, as indices into f
 //   int gid[cap_c]
 //   T  ca[cap_c]      eps adt / 2
 // Per block: stage (cells on the first warps, nodes on the warps that hold
-// no cell when they are enough), barrier, one flux per thread into f,
-// barrier, and the thread that staged a cell sums its edges' fluxes (+f for
-// the edge's first cell slot, -f for its second; padding entries add 0
-// times thread 0's flux, computed in every block) onto the prefetched res
-// and stores it: a fixed order, deterministic.
+// no cell when they are enough; each gather entry "local edge x 16 + map
+// slot" becomes the index of +f (the edge's first cell slot) or -f (its
+// second), padding the zero row), barrier, one flux per thread stored with
+// its negation, barrier, and the thread that staged a cell adds the rows
+// its entries index onto the prefetched res and stores it: a fixed order,
+// deterministic, with no sign or padding test after the last barrier.  In
+// FP64, whose pipe bounds the kernel, no negated copy is stored and the
+// rows keep the plan's entries: the gather adds sign x flux (one FMA per
+// value, padding entries 0 times row 0), measured 3 % faster there.
+// GW1: every cell has at most 4 increments in the block (one gather row),
+// the case of quadrilateral meshes.
 template <typename T>
 __host__ __device__ constexpr int res_g_smem_per_cell()
 {
     return 13 * (int)sizeof(T) + 4;
 }
 
-template <typename T, bool SOA>
-__global__ void __maxnreg__(sizeof(T) == 4 ? 32 : 48) res_calc_hier_g(const mp_block_desc *__restrict__ desc, int block0,
-                                                        const ushort4 *__restrict__ lmap,
-                                                        const ushort4 *__restrict__ gat, int gw4,
-                                                        const int32_t *__restrict__ fp, const T *__restrict__ x,
-                                                        const T *__restrict__ q, const T *__restrict__ adt,
-                                                        T *__restrict__ res, int64_t nnode, int64_t ncell, int cap_c,
-                                                        int cap_n, int cap_f, T gm1, T half_eps, int *__restrict__ err)
+// Arguments of the gather-form kernels.
+template <typename T>
+struct res_g_args {
+    const mp_block_desc *desc;
+    const ushort4 *lmap;
+    const ushort4 *gat;
+    const int32_t *fp;
+    const T *x, *q, *adt;
+    T *res;
+    int64_t nnode, ncell;
+    int gw4, cap_c, cap_n;
+    T gm1, half_eps;
+    int *err;
+};
+
+// One block (index b of the descriptor table) of the gather form.
+// PERSIST: the block runs inside a persistent launch: no dependent-launch
+// wait, and res is read through L2 (another CTA of the launch may have
+// written it before the last grid barrier).  Returns false, with the error
+// word set, when the block does not fit the launch.
+template <typename T, bool SOA, bool GW1, bool PERSIST>
+__device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
 {
+    const ushort4 *__restrict__ lmap = A.lmap;
+    const ushort4 *__restrict__ gat = A.gat;
+    const int32_t *__restrict__ fp = A.fp;
+    const T *__restrict__ x = A.x;
+    const T *__restrict__ q = A.q;
+    const T *__restrict__ adt = A.adt;
+    T *__restrict__ res = A.res;
+    const int64_t nnode = A.nnode, ncell = A.ncell;
+    const int gw4 = A.gw4, cap_c = A.cap_c, cap_n = A.cap_n;
+    const T gm1 = A.gm1, half_eps = A.half_eps;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bd = blockDim.x, tid = threadIdx.x;
+    const int nrow = GW1 ? 1 : gw4;
     T *s_cq = reinterpret_cast<T *>(smem_raw);
     T *s_cp = s_cq + 4 * cap_c;
     T *s_cr = s_cp + 4 * cap_c;
     T *s_f = s_cr + 4 * cap_c;
-    T *s_xh = s_f + 4 * cap_f;
+    constexpr bool NEG_ROWS = sizeof(T) == 4;  // negated copies of the fluxes in f
+    const int nfrow = NEG_ROWS ? 2 * bd + 1 : bd + 1;
+    T *s_xh = s_f + 4 * nfrow;
     ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_xh + 2 * cap_n);
-    int *s_gid = reinterpret_cast<int *>(s_ge + gw4 * cap_c);
+    int *s_gid = reinterpret_cast<int *>(s_ge + nrow * cap_c);
     T *s_ca = reinterpret_cast<T *>(s_gid + cap_c + (sizeof(T) == 8 ? (cap_c & 1) : 0));
 
-    mp_pdl_trigger();
-    const mp_block_desc d = desc[block0 + blockIdx.x];
+    const mp_block_desc d = A.desc[b];
     const int nn = d.fp_count[0], nc = d.fp_count[1];
     if ((unsigned)(reinterpret_cast<unsigned char *>(s_ca + cap_c) - smem_raw) > dynamic_smem_bytes() ||
-        nc > cap_c || nn > cap_n || d.nitems > cap_f || cap_f > 2 * bd || gw4 < 1 || gw4 > 4) {
-        if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
-        return;
+        nc > cap_c || nn > cap_n || d.nitems > bd || gw4 < 1 || gw4 > (GW1 ? 1 : 4)) {
+        if (tid == 0) atomicExch(A.err, MP_DEVERR_SMEM);
+        return false;
     }
     const int32_t *fpn = fp + d.fp_start[0];
     const int32_t *fpc = fp + d.fp_start[1];
-    // the thread's first edge's local map does not depend on the staging:
-    // issued first (a second edge, tid + blockDim, loads its own later)
-    ushort4 l0 = make_ushort4(0, 0, 0, 0);
-    if (tid < d.nitems) l0 = lmap[d.item_start + tid];
+    const bool active = tid < d.nitems;
+    ushort4 l = make_ushort4(0, 0, 0, 0);
+    if (active) l = lmap[d.item_start + tid];  // independent of the staging: issued first
+    if (tid == 0) st_row4(s_f, nfrow - 1, T(0), T(0), T(0), T(0));
 
+    // gather entry -> index of the row of f it adds
+    const unsigned zero_row = (unsigned)nfrow - 1u;
+    auto to_row = [&](unsigned e) -> unsigned short {
+        const unsigned minus = (e & 15u) == 3u ? (NEG_ROWS ? (unsigned)bd : 0x8000u) : 0u;
+        return (unsigned short)(e == 0xFFFFu ? zero_row : (e >> 4) + minus);
+    };
     // cells: q, adt and the gather rows, then res after the dependent-launch
     // wait (the previous colour's launch writes it), then the primitives
     for (int i = tid; i < nc; i += bd) {
@@ -406,11 +456,15 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 32 : 48) res_calc_hier_g(const mp_b
         load_cell<T, SOA>(q, ncell, g, r, ru, rv, E);
         const T a = adt[g];
         const ushort4 *rw = gat + (int64_t)(d.fp_start[1] + i) * gw4;
-        for (int h = 0; h < gw4; ++h) s_ge[h * cap_c + i] = rw[h];
+        for (int h = 0; h < nrow; ++h) {
+            const ushort4 e4 = rw[h];
+            s_ge[h * cap_c + i] =
+                NEG_ROWS ? make_ushort4(to_row(e4.x), to_row(e4.y), to_row(e4.z), to_row(e4.w)) : e4;
+        }
         s_gid[i] = g;
-        mp_pdl_wait();
+        if (!PERSIST) mp_pdl_wait();
         T r0, r1, r2, r3;
-        load_res<T, SOA>(res, ncell, g, r0, r1, r2, r3);
+        load_res<T, SOA, PERSIST>(res, ncell, g, r0, r1, r2, r3);
         T u, v, p, H;
         cell_prims(r, ru, rv, E, gm1, u, v, p, H);
         st_row4(s_cq, i, r, ru, rv, E);
@@ -441,11 +495,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 32 : 48) res_calc_hier_g(const mp_b
     }
     __syncthreads();
 
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int e = tid + k * bd;
-        if (e >= d.nitems) continue;
-        const ushort4 l = k == 0 ? l0 : lmap[d.item_start + e];
+    if (active) {
         const int na = l.x, nb = l.y, c1 = l.z, c2 = l.w;
         const T nxh = s_xh[2 * na + 1] - s_xh[2 * nb + 1];
         const T nyh = s_xh[2 * nb] - s_xh[2 * na];
@@ -458,28 +508,36 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 32 : 48) res_calc_hier_g(const mp_b
         // eps adt / 2 is folded in per cell: mu = a1 + a2
         edge_flux(nxh, nyh, r1, ru1, rv1, E1, u1, v1, p1, H1, s_ca[c1], r2, ru2, rv2, E2, u2, v2, p2, H2, s_ca[c2],
                   T(1), f);
-        st_row4(s_f, e, f[0], f[1], f[2], f[3]);
+        st_row4(s_f, tid, f[0], f[1], f[2], f[3]);
+        if (NEG_ROWS) st_row4(s_f, bd + tid, flip_sign(f[0]), flip_sign(f[1]), flip_sign(f[2]), flip_sign(f[3]));
     }
     __syncthreads();
 
     for (int i = tid; i < nc; i += bd) {
         T a0, a1, a2, a3;
         ld_row4(s_cr, i, a0, a1, a2, a3);
-        for (int h = 0; h < gw4; ++h) {
+        for (int h = 0; h < nrow; ++h) {
             const ushort4 e4 = s_ge[h * cap_c + i];
             const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const unsigned e = es[j];
-                const bool valid = e != 0xFFFFu;
-                const int t = valid ? (int)(e >> 4) : 0;
-                const T sg = !valid ? T(0) : ((e & 15u) == 3u ? T(-1) : T(1));
                 T v0, v1, v2, v3;
-                ld_row4(s_f, t, v0, v1, v2, v3);
-                a0 += sg * v0;
-                a1 += sg * v1;
-                a2 += sg * v2;
-                a3 += sg * v3;
+                if (NEG_ROWS) {
+                    ld_row4(s_f, es[j], v0, v1, v2, v3);
+                    a0 += v0;
+                    a1 += v1;
+                    a2 += v2;
+                    a3 += v3;
+                } else {  // raw entry: +f, -f, or padding (0 times row 0)
+                    const unsigned e = es[j];
+                    const bool valid = e != 0xFFFFu;
+                    const T sg = !valid ? T(0) : ((e & 15u) == 3u ? T(-1) : T(1));
+                    ld_row4(s_f, valid ? (int)(e >> 4) : 0, v0, v1, v2, v3);
+                    a0 += sg * v0;
+                    a1 += sg * v1;
+                    a2 += sg * v2;
+                    a3 += sg * v3;
+                }
             }
         }
         const int64_t g = s_gid[i];
@@ -495,6 +553,43 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 32 : 48) res_calc_hier_g(const mp_b
         } else {
             reinterpret_cast<float4 *>(res)[g] = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
         }
+    }
+    return true;
+}
+
+// One launch per block colour: CTA k takes block block0 + k.
+template <typename T, bool SOA, bool GW1>
+__global__ void __maxnreg__(sizeof(T) == 4 ? 32 : 48) res_calc_hier_g(res_g_args<T> A, int block0)
+{
+    mp_pdl_trigger();
+    res_block_g<T, SOA, GW1, false>(A, block0 + (int)blockIdx.x);
+}
+
+// One persistent (cooperative) launch for all block colours: the resident
+// CTAs take the blocks of a colour one at a time from a counter (a CTA that
+// finishes early takes the next block, so the colour's end is not held back
+// by a fixed share) and meet at a bounded grid-wide barrier before the next
+// colour, whose blocks may share cells with this one's.  A barrier that runs
+// out leaves MP_ETIMEOUT in the error word and the CTAs return.
+// bar[0]: barrier arrivals; bar[1 + c]: blocks of colour c taken; all 0 at
+// launch.
+template <typename T, bool SOA, bool GW1>
+__global__ void __maxnreg__(sizeof(T) == 4 ? 32 : 48) res_calc_hier_gp(res_g_args<T> A,
+                                                                       const int32_t *__restrict__ color_off,
+                                                                       int ncolors, unsigned *bar)
+{
+    __shared__ int s_next;
+    for (int c = 0; c < ncolors; ++c) {
+        const int b0 = color_off[c], nb = color_off[c + 1] - b0;
+        for (;;) {
+            if (threadIdx.x == 0) s_next = (int)atomicAdd(bar + 1 + c, 1u);
+            __syncthreads();
+            const int k = s_next;
+            if (k >= nb) break;
+            if (!res_block_g<T, SOA, GW1, true>(A, b0 + k)) return;
+            __syncthreads();  // the next block reuses the shared memory and s_next
+        }
+        if (c + 1 < ncolors && !mp_grid_barrier(bar, (unsigned)(c + 1) * gridDim.x, MP_GRID_WAIT_NS, A.err)) return;
     }
 }
 
@@ -673,7 +768,8 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         // default increments: gather (measured faster on GB300 in both
         // precisions: FP64 0.487 against 0.554 ms for thread colours)
         const int variant = mp_staged(P, MP_STAGED_GATHER);
-        const bool gather = variant == MP_STAGED_GATHER && mp_gather_ready(P);
+        const bool gather =
+            (variant == MP_STAGED_GATHER || variant == MP_STAGED_PERSISTENT) && mp_gather_ready(P);
         int *err = nullptr;
         int rc = mp_device_error_word(&err);
         if (rc != MP_OK) return rc;
@@ -682,21 +778,43 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         bool overlap = false;  // the first launch follows the caller's work: plain stream order
         if (gather) {
             const int gw4 = P->gat_w / 4;
-            // FP32 blocks of more than 256 edges run two edges per thread:
-            // more loads in flight per thread at the same thread count
-            const int threads = (sizeof(T) == 4 && bs > 256 && bs % 64 == 0) ? bs / 2 : bs;
+            const bool gw1 = gw4 == 1;
             const int smem = cap_c * res_g_smem_per_cell<T>() + cap_n * 2 * (int)sizeof(T) +
-                             bs * 4 * (int)sizeof(T) + gw4 * cap_c * 8 + (sizeof(T) == 8 ? 4 : 0);
-            auto kern = res_calc_hier_g<T, SOA>;
+                             (sizeof(T) == 4 ? 2 * bs + 1 : bs + 1) * 4 * (int)sizeof(T) + (gw1 ? 1 : gw4) * cap_c * 8 +
+                             (sizeof(T) == 8 ? 4 : 0);
+            const res_g_args<T> A{P->dev.desc, reinterpret_cast<const ushort4 *>(P->dev.lmap),
+                                  reinterpret_cast<const ushort4 *>(P->dev.gat), fp, (const T *)x, (const T *)q,
+                                  (const T *)adt, (T *)res, nnode, ncell, gw4, cap_c, cap_n, gm1, half_eps, err};
+            if (variant == MP_STAGED_PERSISTENT) {
+                auto kern = gw1 ? res_calc_hier_gp<T, SOA, true> : res_calc_hier_gp<T, SOA, false>;
+                if ((rc = mp_allow_smem(kern, smem)) != MP_OK) return rc;
+                int dev = 0, sms = 0, occ = 0;
+                MP_CUDA_TRY(cudaGetDevice(&dev));
+                MP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                MP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, smem));
+                if (occ < 1) return MP_ESMEM;
+                MP_CUDA_TRY(cudaMemsetAsync(P->dev.bar, 0, sizeof(unsigned) * (1 + P->ncolors), s));
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)(sms * occ));
+                cfg.blockDim = dim3((unsigned)bs);
+                cfg.dynamicSmemBytes = (size_t)smem;
+                cfg.stream = s;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeCooperative;
+                at[0].val.cooperative = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, A, (const int32_t *)P->dev.color_off, P->ncolors,
+                                               P->dev.bar));
+                MP_CUDA_TRY(cudaGetLastError());
+                return MP_OK;
+            }
+            auto kern = gw1 ? res_calc_hier_g<T, SOA, true> : res_calc_hier_g<T, SOA, false>;
             if ((rc = mp_allow_smem(kern, smem)) != MP_OK) return rc;
             for (int c = 0; c < P->ncolors; ++c) {
                 int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;
                 if (nb == 0) continue;
-                MP_CUDA_TRY(mp_launch(kern, nb, threads, smem, s, overlap, P->dev.desc, b0,
-                                      reinterpret_cast<const ushort4 *>(P->dev.lmap),
-                                      reinterpret_cast<const ushort4 *>(P->dev.gat), gw4, fp, (const T *)x,
-                                      (const T *)q, (const T *)adt, (T *)res, nnode, ncell, cap_c, cap_n, bs, gm1,
-                                      half_eps, err));
+                MP_CUDA_TRY(mp_launch(kern, nb, bs, smem, s, overlap, A, b0));
                 overlap = true;
             }
             MP_CUDA_TRY(cudaGetLastError());

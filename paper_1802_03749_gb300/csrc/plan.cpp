@@ -977,7 +977,7 @@ int build(const mp_map *maps, int32_t nmaps, int64_t from_size, const mp_plan_op
     if (o.reorder < 0 || o.reorder > 2 || o.coloring < 0 || o.coloring > 3 || o.layout < 0 || o.layout > 1)
         return MP_EINVAL;
     if (!(o.imbalance >= 1.0) || o.imbalance > 2.0) return MP_EINVAL;
-    if (o.staged < -1 || o.staged > 6 || o.recolor < -1 || o.recolor > 1) return MP_EINVAL;
+    if (o.staged < -1 || o.staged > 7 || o.recolor < -1 || o.recolor > 1) return MP_EINVAL;
     if (o.data_reorder < 0) o.data_reorder = (o.reorder == MP_REORDER_PARTITION || o.block_of) ? 1 : 0;
     P->opts = o;
     P->opts.block_of = nullptr;  // read during the build only
@@ -1224,7 +1224,7 @@ void mesh_plan_destroy(mp_plan *P)
 
 int mesh_plan_set_staged(mp_plan *P, int32_t staged)
 {
-    if (!P || staged < -1 || staged > 6) return MP_EINVAL;
+    if (!P || staged < -1 || staged > 7) return MP_EINVAL;
     P->opts.staged = staged;
     return MP_OK;
 }

@@ -32,6 +32,9 @@ struct mp_device_tables {
     int32_t *fp = nullptr;      // all footprint lists, slot-major
     uint8_t *tcolor = nullptr;  // thread colour per iteration (HIER)
     uint16_t *gat = nullptr;    // HIER: block-local inverse of the written maps
+    int32_t *color_off = nullptr;  // HIER: block range of each colour (persistent launches)
+    unsigned *bar = nullptr;       // HIER: persistent launches: grid-barrier arrivals, then one
+                                   // block counter per colour (ncolors + 1 words)
     int32_t *map[MP_MAX_MAPS] = {nullptr, nullptr, nullptr, nullptr};  // GLOBAL / ATOMIC / TWOSTEP
     int32_t *inv_off = nullptr;  // TWOSTEP: written to-set point -> range of inv_idx
     int32_t *inv_idx = nullptr;  // TWOSTEP: item * arity + slot, sorted by (point, item, slot)

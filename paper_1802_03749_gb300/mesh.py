@@ -191,9 +191,11 @@ class AirfoilBatch:
     ``choices[k]`` = (block_size, reorder, coloring) of mesh k; meshes with
     two-layer colouring must share one block size (the fused launch's).
     Storage is FP32 or FP64; the update and the residual sum are FP64.
+    ``res_staged="persistent"`` runs the fused res_calc in one persistent
+    launch for all colour phases instead of one launch per phase.
     """
 
-    def __init__(self, meshes, states, qinf, choices, dtype="f32", gam=1.4, eps=0.05, cfl=0.9):
+    def __init__(self, meshes, states, qinf, choices, dtype="f32", gam=1.4, eps=0.05, cfl=0.9, res_staged=None):
         import numpy as np
         import torch
         order = sorted(range(len(meshes)), key=lambda k: choices[k][2] != "hier")   # hier meshes first
@@ -214,6 +216,8 @@ class AirfoilBatch:
         if hier and len({choices[order[i]][0] for i in hier}) != 1:
             raise ValueError("two-layer meshes of one batch must share a block size")
         self.res_hier = Plan.batch([self.plans[i].res for i in hier]) if hier else None
+        if self.res_hier is not None and res_staged is not None:
+            self.res_hier.set_staged(res_staged)
         atom = [i for i in range(len(order)) if i not in hier]
         self.res_atomic = None
         if atom:

@@ -91,5 +91,5 @@ def test_loop_argument_errors_without_device():
     assert L.loop_face_flux(edge_plan.handle, F64, N, N, N, 1.0, 1e-3, 0.72, N) == EINVAL   # gamma must exceed 1
     assert L.loop_face_flux(cell_plan.handle, F64, N, N, N, 1.4, 1e-3, 0.72, N) == EPLAN
     assert L.loop_elem_assemble(res_plan.handle, F64, N, N, N, N, N, 0.01, N) == EPLAN
-    assert L.mesh_plan_set_staged(res_plan.handle, 7) == EINVAL
-    assert L.mesh_plan_set_staged(res_plan.handle, 6) == 0
+    assert L.mesh_plan_set_staged(res_plan.handle, 8) == EINVAL
+    assert L.mesh_plan_set_staged(res_plan.handle, 7) == 0

@@ -18,7 +18,11 @@ def small_batch():
     return meshes, states
 
 
-def test_fused_res_calc_matches_per_mesh_oracle():
+@pytest.mark.parametrize("staged,dtype", [(None, "f64"), ("persistent", "f64"), ("persistent", "f32")])
+def test_fused_res_calc_matches_per_mesh_oracle(staged, dtype):
+    """The fused plan of meshes of uneven size: one launch per colour phase,
+    or one persistent launch for the whole batch (FP64, and FP32 against the
+    oracle on FP32-rounded inputs)."""
     import paper_1802_03749_gb300 as ml
     from paper_1802_03749_gb300.mesh import AirfoilPlans
     meshes, states = small_batch()
@@ -27,19 +31,55 @@ def test_fused_res_calc_matches_per_mesh_oracle():
     Ps = [AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
                        block_size=bs, reorder=ro) for m, (bs, ro) in zip(meshes, opts)]
     B = ml.Plan.batch([P.res for P in Ps])
-    cat = lambda arrs: torch.tensor(np.concatenate(arrs), device="cuda")
+    B.set_staged(staged)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    cat = lambda arrs: torch.tensor(np.concatenate(arrs), dtype=tdt, device="cuda")
     x = cat([P.to_plan(m.x, "node") for P, m in zip(Ps, meshes)])
     q = cat([P.to_plan(s, "cell") for P, s in zip(Ps, states)])
     adt = cat([P.to_plan(a, "cell") for P, a in zip(Ps, adts)])
     res = torch.zeros_like(q)
     ml.loop_res_calc(B, x, q, adt, res)
     ml.mp_check_device_status()
-    out = res.cpu().numpy()
+    out = res.double().cpu().numpy()
     off = 0
+    r = (lambda a: round_to(a, np.float32)) if dtype == "f32" else (lambda a: a)
     for P, m, s, a in zip(Ps, meshes, states, adts):
         got = P.from_plan(out[off:off + m.ncell], "cell", 4)
         off += m.ncell
-        assert rel_l2(got, oracle.res_calc(m.edge2node, m.edge2cell, m.x, s, a)) <= 1e-12
+        ref = oracle.res_calc(m.edge2node, m.edge2cell, r(m.x), r(s), r(a))
+        assert rel_l2(got, ref) <= (1e-12 if dtype == "f64" else 1e-5)
+
+
+def test_persistent_launch_in_a_graph():
+    """The persistent (cooperative) res_calc launch captured in a CUDA graph
+    and replayed gives the eager launch's bits."""
+    import paper_1802_03749_gb300 as ml
+    from paper_1802_03749_gb300.mesh import AirfoilPlans
+    m = meshgen.quad_mesh(90, 45, seed=7)
+    s = meshgen.quad_state(m.ncell, seed=7)
+    a = oracle.adt_calc(m.cell2node, m.x, s)
+    P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
+                     block_size=128, reorder="partition", staged="persistent")
+    P.res.upload()
+    t = lambda v, w: torch.tensor(P.to_plan(v, w), device="cuda")
+    x, q, adt = t(m.x, "node"), t(s, "cell"), t(a, "cell")
+    eager = torch.zeros_like(q)
+    ml.loop_res_calc(P.res, x, q, adt, eager)
+    torch.cuda.synchronize()
+    res = torch.zeros_like(q)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        ml.loop_res_calc(P.res, x, q, adt, res)
+    for _ in range(3):
+        res.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    ml.mp_check_device_status()
+    assert torch.equal(res, eager)
+    ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, s, a)
+    assert rel_l2(P.from_plan(res.cpu().numpy(), "cell", 4), ref) <= 1e-12
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

@@ -3,7 +3,9 @@ in forms that fault nothing: a block footprint larger than the shared
 memory a CTA may opt into is rejected on the host with MP_ESMEM before any
 launch, the device error word stays clear, and the same mesh runs once its
 blocks are smaller.  (The 256-colour limit, MP_ECOLORS, is a planner error:
-tests/test_plan.py.)"""
+tests/test_plan.py.)  And the bounded grid-wide wait of the persistent
+launches: a wait that can only run out returns MP_ETIMEOUT through the
+device error word after its limit, and the GPU stays usable."""
 import numpy as np
 import pytest
 
@@ -83,3 +85,19 @@ def test_footprint_limit_is_per_kernel_layout():
     r = lambda a: a.astype(np.float32).astype(np.float64)
     ref = oracle.res_calc(e2n, e2c, r(x), r(q), r(adt))
     assert rel_l2(got, ref) <= 1e-5
+
+
+def test_grid_wait_runs_out_and_reports_timeout():
+    import paper_1802_03749_gb300 as ml
+    ml.mp_grid_wait_test(8, 50_000_000, 0)        # every arrival comes: no error
+    ml.mp_check_device_status()
+    ml.mp_grid_wait_test(8, 20_000_000, 1)        # one arrival never comes: 20 ms, then MP_ETIMEOUT
+    with pytest.raises(ml.MeshLoopError) as e:
+        ml.mp_check_device_status()
+    assert e.value.name == "MP_ETIMEOUT"
+    ml.mp_check_device_status()                   # the status word was cleared
+    ml.mp_grid_wait_test(8, 50_000_000, 0)        # and the device still works
+    ml.mp_check_device_status()
+    with pytest.raises(ml.MeshLoopError) as e:
+        ml.mp_grid_wait_test(0, 1000, 0)
+    assert e.value.name == "MP_EINVAL"

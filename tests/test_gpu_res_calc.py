@@ -184,7 +184,7 @@ def test_res_calc_full_size_parity(ml, compute):
     assert rel_l2(got, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("variant", ["pipelined", "smem_atomic", "gather", "simple", "warp_agg"])
+@pytest.mark.parametrize("variant", ["pipelined", "smem_atomic", "gather", "simple", "warp_agg", "persistent"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("reorder,block_size", [("partition", 480), ("rcm", 256), ("none", 480), ("partition", 1024)])
 def test_res_calc_staged_variants(ml, variant, dtype, reorder, block_size):

@@ -42,20 +42,31 @@ def test_step_fp64_10_steps(layout, coloring, reorder):
 
 
 def test_step_fp32_error_per_step():
-    """FP32 storage and arithmetic, FP64 update and residual sum: error of q
-    against the FP64 oracle stays below 1e-5 rel-L2 over 10 steps."""
+    """FP32 storage and arithmetic, FP64 update and residual sum, against the
+    FP64 oracle started from the same FP32-rounded state, per field (rho,
+    rho u, rho v, E) and per step over 10 steps: each field's rel-L2 stays
+    below 1e-5, the accumulated change q_k - q_0 of each field below 1e-4
+    (it is a small difference of stored values), the RMS residual below
+    1e-4 relative."""
     m, q, qinf, S = make("aos", "f32")
-    qo = round_to(q, np.float32).copy()
-    errs = []
+    q0 = round_to(q, np.float32)
+    qo = q0.copy()
+    rows = []
     for k in range(10):
         S.rms.zero_()
         S.step()
         torch.cuda.synchronize()
         rms_ref, _ = oracle.step(m, qo, qinf)
         rms = float(np.sqrt(S.rms.item() / m.ncell))
-        errs.append((rel_l2(S.q_original(), qo), abs(rms - rms_ref) / rms_ref))
-    assert max(e[0] for e in errs) <= 1e-5, errs
-    assert max(e[1] for e in errs) <= 1e-4, errs
+        got = S.q_original()
+        per_field = [rel_l2(got[:, f], qo[:, f]) for f in range(4)]
+        change = [rel_l2(got[:, f] - q0[:, f], qo[:, f] - q0[:, f]) for f in range(4)]
+        rows.append((k + 1, per_field, change, abs(rms - rms_ref) / rms_ref))
+    for step, per_field, change, rms_err in rows:
+        assert max(per_field) <= 1e-5, (step, per_field)
+        assert max(change) <= 1e-4, (step, change)
+        assert rms_err <= 1e-4, (step, rms_err)
+    assert rel_l2(S.q_original(), qo) <= 1e-5
 
 
 def test_step_graph_replay_matches_eager():
