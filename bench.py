@@ -51,6 +51,10 @@ MIN_CALLS = 100
 MIN_WARMUP = 10
 MIN_REP_SECONDS = 0.1
 FIELDS = ("rho", "rho_u", "rho_v", "E")
+# block size S of the two-layer plans per arithmetic, the fastest measured on
+# the 2400x1200 pass (FP64: 0.496 / 0.487 / 0.483 / 0.478 / 0.492 ms at S =
+# 192 / 256 / 320 / 384 / 512; double-word and FP32: 256)
+BLOCK_DEFAULT = {"f64": 384, "dw": 256, "f32": 256}
 
 # algorithmic floating-point operations of one interior edge as the oracle
 # evaluates it: two normal fluxes of 20 (pressure 7, normal velocity 4,
@@ -94,7 +98,8 @@ def read_traffic(compute, staged, args):
             if "=" in line and not line.startswith("#"):
                 k, v = line.strip().split("=", 1)
                 rec[k.strip()] = v.strip()
-    want = {"compute": compute, "staged": staged, "block": str(args.block_size), "layout": args.layout}
+    want = {"compute": compute, "staged": staged, "block": str(args.block_size or BLOCK_DEFAULT[compute]),
+            "layout": args.layout}
     if any(rec.get(k) != v for k, v in want.items()):
         return None, "recorded for another launch configuration"
     if rec.get("sources_sha256") != sources_sha256():
@@ -133,7 +138,8 @@ def record_traffic(args):
                 f"# {args.nx}x{args.ny} quads, from {n} consecutive launches captured with ncu --cache-control none\n"
                 f"# (dirty lines of one launch are written back during the following ones, so writes are counted).\n"
                 f"# command: {args.record_command}\n")
-        for k, v in (("compute", args.compute), ("staged", staged), ("block", args.block_size),
+        for k, v in (("compute", args.compute), ("staged", staged),
+                     ("block", args.block_size or BLOCK_DEFAULT[args.compute]),
                      ("layout", args.layout), ("nx", args.nx), ("ny", args.ny), ("launches_captured", n),
                      ("launches_per_pass", lpp), ("read_bytes_per_pass", int(round(rd * lpp / n))),
                      ("write_bytes_per_pass", int(round(wr * lpp / n))),
@@ -803,7 +809,8 @@ def main():
                     help="least calls per timed repetition (raised to 100 and to 0.1 s per repetition)")
     ap.add_argument("--warmup", type=int, default=MIN_WARMUP, help="warm-up calls (at least 10)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--block-size", type=int, default=256)
+    ap.add_argument("--block-size", type=int, default=None,
+                    help="block size S of the two-layer plans (default: 384 for FP64, 256 otherwise)")
     ap.add_argument("--layout", default="aos", choices=["aos", "soa"])
     ap.add_argument("--staged", default=None,
                     choices=["simple", "gather", "smem_atomic", "pipelined", "warp_agg", "persistent"],
@@ -865,9 +872,9 @@ def main():
     tdt_of = {"f64": torch.float64, "dw": torch.float64, "f32": torch.float32}
     elt_of = {"f64": 8, "dw": 8, "f32": 4}
 
-    def make_plan(coloring, reorder, layout=args.layout, first_fit=False, staged=None):
+    def make_plan(coloring, reorder, layout=args.layout, first_fit=False, staged=None, bs=256):
         P = AirfoilPlans(m.ncell, m.nnode, m.edge2node, m.edge2cell, m.bedge2node, m.bedge2cell, m.cell2node,
-                         block_size=args.block_size, reorder=reorder, coloring=coloring, layout=layout,
+                         block_size=bs, reorder=reorder, coloring=coloring, layout=layout,
                          staged=staged, recolor=0 if first_fit else -1)
         P.res.upload()
         return P
@@ -913,7 +920,8 @@ def main():
     elt = elt_of[compute]
     useful = useful_bytes_res_calc(m.ncell, m.nnode, m.nedge, elt)
     head_staged = args.staged or default_staged(compute)
-    P = make_plan("hier", "partition")
+    head_bs = args.block_size or BLOCK_DEFAULT[compute]
+    P = make_plan("hier", "partition", bs=head_bs)
     P.res.set_staged(head_staged)
     st = P.res.stats()
     d = make_data(P, compute)
@@ -949,6 +957,10 @@ def main():
         # the data reuse measure of the plan: useful bytes / DRAM bytes per pass
         roof["useful_over_dram"] = useful / tr["bytes_per_pass"]
         roof["achieved_dram_gbs"] = tr["bytes_per_pass"] / (ms_step * 1e-3) / 1e9
+        # DRAM reads over the useful reads (x, q, adt, res, maps as int32):
+        # above 1 by the plan tables and the re-read halo of shared points
+        useful_reads = useful - 4 * m.ncell * elt
+        roof["read_amplification"] = tr["read_bytes_per_pass"] / useful_reads
 
     # ---------------------------------------------------------- e2e (host buffers)
     # through the C-ABI call with host arrays (loop_res_calc_host): every step
@@ -996,17 +1008,20 @@ def main():
         "block_colors": st["nblock_colors"], "thread_colors_mean": st["mean_thread_colors"],
         "reuse": st["reuse_all"], "plan_seconds": st["seconds_total"], "parity": head_parity}}
     if not args.no_variants:
-        plans = {("hier", "partition", args.layout, False): P}
+        plans = {("hier", "partition", args.layout, False, head_bs): P}
         pick = set(args.variants.split(",")) if args.variants else None
         for key, name, comp_v, staged in res_variants(compute):
-            if name == head_name and key == ("hier", "partition", args.layout, False):
+            # two-layer plans at their arithmetic's block size; the one-thread-
+            # per-iteration baselines do not depend on it
+            key = key + ((args.block_size or BLOCK_DEFAULT[comp_v]) if key[0] == "hier" else 256,)
+            if name == head_name and key == ("hier", "partition", args.layout, False, head_bs):
                 continue
             if pick is not None and name not in pick:
                 continue
             try:
                 if key not in plans:
                     plans.clear()   # plans are visited grouped: free the previous one
-                    plans[key] = make_plan(key[0], key[1], layout=key[2], first_fit=key[3])
+                    plans[key] = make_plan(key[0], key[1], layout=key[2], first_fit=key[3], bs=key[4])
                 Pv = plans[key]
                 if key[0] == "hier":
                     Pv.res.set_staged(staged)
@@ -1041,7 +1056,7 @@ def main():
                        "implementation": ("double-word arithmetic, " if compute == "dw" else "")
                                          + "two-layer colouring"
                                          + f" ({'thread-coloured' if head_staged == 'simple' else head_staged}"
-                                         + f" increments), RCM + partition, block {args.block_size}, "
+                                         + f" increments), RCM + partition, block {head_bs}, "
                                          + args.layout.upper(),
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (useful bytes {useful / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB); "

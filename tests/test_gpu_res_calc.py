@@ -156,14 +156,14 @@ def test_res_calc_double_word_scaled_inputs(ml, xs, qs):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("compute", ["f64", "f64_480", "dw", "dw_colour", "dw_global", "dw_atomic", "f32"])
+@pytest.mark.parametrize("compute", ["f64", "f64_colour", "dw", "dw_colour", "dw_global", "dw_atomic", "f32"])
 def test_res_calc_full_size_parity(ml, compute):
     """The benchmark's workload: 2400x1200 quads, two-layer colouring,
-    RCM + partition, AoS at block 256 (the benchmark's launch): native FP64
-    with thread-coloured increments (the headline), double-word arithmetic
-    (gather and thread colours) and FP32 (gather); native FP64 at block 480;
-    the double-word global-colour and atomic baselines on the RCM order.
-    The oracle computes every cell."""
+    RCM + partition, AoS, in the benchmark's launches: native FP64 at block
+    384 with gather increments (the headline), double-word arithmetic
+    (gather and thread colours) and FP32 (gather) at block 256; native FP64
+    with thread colours at block 480; the double-word global-colour and
+    atomic baselines on the RCM order.  The oracle computes every cell."""
     m, q, adt = case(2400, 1200)
     if compute == "dw":
         got = run_dw(ml, m, q, adt, "partition", "aos", block_size=256)
@@ -177,9 +177,10 @@ def test_res_calc_full_size_parity(ml, compute):
                               round_to(adt, np.float32))
         assert rel_l2(got, ref) <= 1e-5
         return
+    elif compute == "f64":
+        got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64", block_size=384)
     else:
-        got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64",
-                              block_size=256 if compute == "f64" else 480, staged="simple")
+        got, _ = run_res_calc(ml, m, q, adt, "hier", "partition", "aos", "f64", block_size=480, staged="simple")
     ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
     assert rel_l2(got, ref) <= 1e-12
 
