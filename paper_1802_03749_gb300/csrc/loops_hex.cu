@@ -5,9 +5,11 @@
 //
 // Variants (plan colouring): HIER stages the block's node footprint (x, v)
 // in shared memory and applies the 24 increments per element one thread
-// colour at a time, then writes each footprint node back once; GLOBAL runs
-// one launch per element colour with direct global read-add-writes; ATOMIC
-// uses atomicAdd on f.
+// colour at a time (hex_hier), with shared-memory atomics (hex_hier_c, the
+// compact element terms) or warp-aggregated atomics, then writes each
+// footprint node back once; GLOBAL runs one launch per element colour with
+// direct global read-add-writes and ATOMIC uses atomicAdd on f (both
+// hex_direct_c); TWOSTEP writes per-corner forces for a gather.
 #include "common.cuh"
 
 namespace {
@@ -110,8 +112,8 @@ __device__ __forceinline__ void load3(const T *__restrict__ p, int64_t n, int64_
     }
 }
 
-// smem per footprint node: one record of 8 values (x[3], v[0] | v[1], v[2],
-// two unused), read with two vector loads per corner; f (prefetched,
+// smem per footprint node: one record of 8 values (x, y, z, - | vx, vy, vz,
+// -), read with one vector load per position or velocity; f (prefetched,
 // incremented)[3] and the global id
 template <typename T>
 __host__ __device__ constexpr int hex_smem_per_node()
@@ -119,43 +121,136 @@ __host__ __device__ constexpr int hex_smem_per_node()
     return 11 * (int)sizeof(T) + 4;
 }
 
-// A node record of 8 values in shared memory (16-byte aligned): x, y, z,
-// vx | vy, vz, -, -.
+// A node record of 8 values in shared memory (16-byte aligned).
 template <typename T>
 __device__ __forceinline__ void st_node_rec(T *rec, int i, const T xv[6])
 {
     if (sizeof(T) == 8) {
         double2 *p = reinterpret_cast<double2 *>(rec) + 4 * i;
         p[0] = make_double2((double)xv[0], (double)xv[1]);
-        p[1] = make_double2((double)xv[2], (double)xv[3]);
-        p[2] = make_double2((double)xv[4], (double)xv[5]);
+        p[1] = make_double2((double)xv[2], 0.0);
+        p[2] = make_double2((double)xv[3], (double)xv[4]);
+        p[3] = make_double2((double)xv[5], 0.0);
     } else {
         float4 *p = reinterpret_cast<float4 *>(rec) + 2 * i;
-        p[0] = make_float4((float)xv[0], (float)xv[1], (float)xv[2], (float)xv[3]);
-        p[1] = make_float4((float)xv[4], (float)xv[5], 0.f, 0.f);
+        p[0] = make_float4((float)xv[0], (float)xv[1], (float)xv[2], 0.f);
+        p[1] = make_float4((float)xv[3], (float)xv[4], (float)xv[5], 0.f);
+    }
+}
+// half h of record i: 0 the position, 1 the velocity
+template <typename T>
+__device__ __forceinline__ void ld_node_half(const T *rec, int i, int h, T o[3])
+{
+    if (sizeof(T) == 8) {
+        const double2 *p = reinterpret_cast<const double2 *>(rec) + 4 * i + 2 * h;
+        const double2 a = p[0], b = p[1];
+        o[0] = (T)a.x;
+        o[1] = (T)a.y;
+        o[2] = (T)b.x;
+    } else {
+        const float4 a = reinterpret_cast<const float4 *>(rec)[2 * i + h];
+        o[0] = (T)a.x;
+        o[1] = (T)a.y;
+        o[2] = (T)a.z;
     }
 }
 template <typename T>
 __device__ __forceinline__ void ld_node_rec(const T *rec, int i, T xe[3], T ve[3])
 {
-    if (sizeof(T) == 8) {
-        const double2 *p = reinterpret_cast<const double2 *>(rec) + 4 * i;
-        const double2 a = p[0], b = p[1], c = p[2];
-        xe[0] = (T)a.x;
-        xe[1] = (T)a.y;
-        xe[2] = (T)b.x;
-        ve[0] = (T)b.y;
-        ve[1] = (T)c.x;
-        ve[2] = (T)c.y;
-    } else {
-        const float4 *p = reinterpret_cast<const float4 *>(rec) + 2 * i;
-        const float4 a = p[0], b = p[1];
-        xe[0] = (T)a.x;
-        xe[1] = (T)a.y;
-        xe[2] = (T)a.z;
-        ve[0] = (T)a.w;
-        ve[1] = (T)b.x;
-        ve[2] = (T)b.y;
+    ld_node_half(rec, i, 0, xe);
+    ld_node_half(rec, i, 1, ve);
+}
+
+// The element quantities the corner forces need, in the compact form that
+// keeps few values alive (the same algebra as hex_element): with C =
+// cof(J) and B_i = C xi_i,
+//   stress   f_i[a] = -s_a B_i[a] = sum_b xi_i[b] t[a][b],  t[a][b] = -s_a C[a][b]
+//   hourglass g_{k,i} = Gamma_{k,i} - (xi_i . w_k) / V,    w_k[b] = sum_a h_k[a] C[a][b],
+//            h_k = sum_j Gamma_{k,j} x_j,  q_k = kappa sum_j g_{k,j} v_j,
+//   f_i -= sum_k g_{k,i} q_k.
+// Vel(j, v) gives corner j's velocity.  Returns V = 8 det J; iV = 1/V.
+template <typename T, typename FV>
+__device__ __forceinline__ T hex_terms(const T xe[8][3], FV Vel, T s0, T s1, T s2, T kappa, T t[3][3], T w[4][3],
+                                       T qk[4][3], T &iV)
+{
+    T J[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T j0 = T(0), j1 = T(0), j2 = T(0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            j0 += sx(i) > 0 ? xe[i][a] : -xe[i][a];
+            j1 += sy(i) > 0 ? xe[i][a] : -xe[i][a];
+            j2 += sz(i) > 0 ? xe[i][a] : -xe[i][a];
+        }
+        J[a][0] = T(0.125) * j0;
+        J[a][1] = T(0.125) * j1;
+        J[a][2] = T(0.125) * j2;
+    }
+    T C[3][3];
+    C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const T V = T(8) * (J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2]);
+    iV = T(1) / V;
+    const T sg[3] = {s0, s1, s2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) t[a][b] = -sg[a] * C[a][b];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int G[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            G[j] = k == 0 ? sy(j) * sz(j) : (k == 1 ? sx(j) * sz(j) : (k == 2 ? sx(j) * sy(j) : sx(j) * sy(j) * sz(j)));
+        T h[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) h[a] += G[j] > 0 ? xe[j][a] : -xe[j][a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) w[k][b] = h[0] * C[0][b] + h[1] * C[1][b] + h[2] * C[2][b];
+        T Q[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const T xb = (sx(j) > 0 ? w[k][0] : -w[k][0]) + (sy(j) > 0 ? w[k][1] : -w[k][1]) +
+                         (sz(j) > 0 ? w[k][2] : -w[k][2]);
+            const T gj = T(G[j]) - xb * iV;
+            T vj[3];
+            Vel(j, vj);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Q[a] += gj * vj[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) qk[k][a] = kappa * Q[a];
+    }
+    return V;
+}
+
+// Force on corner i from the compact terms.
+template <typename T>
+__device__ __forceinline__ void hex_corner(int i, const T t[3][3], const T w[4][3], const T qk[4][3], T iV, T fa[3])
+{
+    T gi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int Gk = k == 0 ? sy(i) * sz(i) : (k == 1 ? sx(i) * sz(i) : (k == 2 ? sx(i) * sy(i) : sx(i) * sy(i) * sz(i)));
+        const T xb = (sx(i) > 0 ? w[k][0] : -w[k][0]) + (sy(i) > 0 ? w[k][1] : -w[k][1]) +
+                     (sz(i) > 0 ? w[k][2] : -w[k][2]);
+        gi[k] = T(Gk) - xb * iV;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T st = (sx(i) > 0 ? t[a][0] : -t[a][0]) + (sy(i) > 0 ? t[a][1] : -t[a][1]) +
+                     (sz(i) > 0 ? t[a][2] : -t[a][2]);
+        fa[a] = st - (gi[0] * qk[0][a] + gi[1] * qk[1][a] + gi[2] * qk[2][a] + gi[3] * qk[3][a]);
     }
 }
 
@@ -282,49 +377,6 @@ __global__ void __launch_bounds__(512) hex_hier(const mp_block_desc *__restrict_
     }
 }
 
-template <typename T, bool SOA, bool ATOMIC>
-__global__ void __launch_bounds__(256) hex_direct(int e0, int e1, const int32_t *__restrict__ e2n,
-                                                  const T *__restrict__ x, const T *__restrict__ v,
-                                                  const T *__restrict__ sig, T *__restrict__ f, T *__restrict__ vol,
-                                                  int64_t nnode, int64_t nelem, T kappa)
-{
-    mp_pdl_trigger();
-    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= e1) return;
-    int nd[8];
-    const int4 *row = reinterpret_cast<const int4 *>(e2n) + 2 * (int64_t)e;
-    int4 r0 = row[0], r1 = row[1];
-    nd[0] = r0.x;
-    nd[1] = r0.y;
-    nd[2] = r0.z;
-    nd[3] = r0.w;
-    nd[4] = r1.x;
-    nd[5] = r1.y;
-    nd[6] = r1.z;
-    nd[7] = r1.w;
-    T xe[8][3], ve[8][3], fe[8][3];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        load3<T, SOA>(x, nnode, nd[i], xe[i][0], xe[i][1], xe[i][2]);
-        load3<T, SOA>(v, nnode, nd[i], ve[i][0], ve[i][1], ve[i][2]);
-    }
-    T s0, s1, s2, V;
-    load3<T, SOA>(sig, nelem, e, s0, s1, s2);
-    hex_element(xe, ve, s0, s1, s2, kappa, fe, V);
-    vol[e] = V;
-    if (!ATOMIC) mp_pdl_wait();  // f: read-add-written by the previous colour's launch
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int64_t j = SOA ? a * nnode + nd[i] : 3 * (int64_t)nd[i] + a;
-            if (ATOMIC)
-                atomicAdd(f + j, fe[i][a]);
-            else
-                f[j] += fe[i][a];
-        }
-}
-
 // Step 1 of the temporary-array method (Sec. 2.1): element e's force on
 // its corner i goes to scratch[(8e + i) * 3 + a]; vol is written directly.
 template <typename T, bool SOA>
@@ -355,6 +407,140 @@ __global__ void __launch_bounds__(256) hex_step1(int n, const int32_t *__restric
         for (int a = 0; a < 3; ++a) o[3 * i + a] = fe[i][a];
 }
 
+// Staged two-layer kernel with the compact element terms and shared-memory
+// atomic increments (blocks of at most 256 elements): per element the
+// positions are held in registers, the velocities read from the node
+// records as the hourglass rates need them, and the 24 corner forces formed
+// one corner at a time from the terms; fewer registers than hex_hier (85
+// against 128 in FP32: 3 CTAs of 256 per SM instead of 2, measured faster
+// than 4 with spills; in FP64 the same 128 without hex_hier's ~1 KB of
+// spills).
+template <typename T, bool SOA>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) hex_hier_c(
+    const mp_block_desc *__restrict__ desc, int block0, const uint4 *__restrict__ lmap,
+    const uint8_t *__restrict__ /* thread colours: not used */, const int32_t *__restrict__ fp,
+    const T *__restrict__ x, const T *__restrict__ v, const T *__restrict__ sig, T *__restrict__ f,
+    T *__restrict__ vol, int64_t nnode, int64_t nelem, int cap, T kappa, int *__restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_xv = reinterpret_cast<T *>(smem_raw);  // [cap][8] node records
+    T *s_f = s_xv + 8 * cap;                    // [3][cap]
+    int *s_gid = reinterpret_cast<int *>(s_f + 3 * cap);
+
+    mp_pdl_trigger();
+    const mp_block_desc d = desc[block0 + blockIdx.x];
+    const int tid = threadIdx.x;
+    const int nn = d.fp_count[0];
+    if ((unsigned)(reinterpret_cast<unsigned char *>(s_gid + cap) - smem_raw) > dynamic_smem_bytes() || nn > cap ||
+        d.nitems > (int)blockDim.x) {
+        if (tid == 0) atomicExch(err, MP_DEVERR_SMEM);
+        return;
+    }
+    const int32_t *fpn = fp + d.fp_start[0];
+    const bool active = tid < d.nitems;
+    uint4 l = make_uint4(0, 0, 0, 0);
+    if (active) l = lmap[d.item_start + tid];
+    // nodes, two per thread and pass, both nodes' loads in flight together;
+    // f (written by the previous colour's launch) after the dependent wait
+    for (int i0 = tid; i0 < nn; i0 += 2 * (int)blockDim.x) {
+        const int i1 = i0 + (int)blockDim.x;
+        const bool two = i1 < nn;
+        const int g0 = fpn[i0], g1 = two ? fpn[i1] : g0;
+        T xv0[6], xv1[6];
+        load3<T, SOA>(x, nnode, g0, xv0[0], xv0[1], xv0[2]);
+        load3<T, SOA>(v, nnode, g0, xv0[3], xv0[4], xv0[5]);
+        if (two) {
+            load3<T, SOA>(x, nnode, g1, xv1[0], xv1[1], xv1[2]);
+            load3<T, SOA>(v, nnode, g1, xv1[3], xv1[4], xv1[5]);
+        }
+        st_node_rec(s_xv, i0, xv0);
+        s_gid[i0] = g0;
+        if (two) {
+            st_node_rec(s_xv, i1, xv1);
+            s_gid[i1] = g1;
+        }
+        mp_pdl_wait();
+        T f0[3], f1[3];
+        load3<T, SOA>(f, nnode, g0, f0[0], f0[1], f0[2]);
+        if (two) load3<T, SOA>(f, nnode, g1, f1[0], f1[1], f1[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s_f[a * cap + i0] = f0[a];
+            if (two) s_f[a * cap + i1] = f1[a];
+        }
+    }
+    __syncthreads();
+    if (active) {
+        const int e = d.item_start + tid;
+        const int loc[8] = {(int)(l.x & 0xffff), (int)(l.x >> 16), (int)(l.y & 0xffff), (int)(l.y >> 16),
+                            (int)(l.z & 0xffff), (int)(l.z >> 16), (int)(l.w & 0xffff), (int)(l.w >> 16)};
+        T xe[8][3];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ld_node_half(s_xv, loc[i], 0, xe[i]);
+        T s0, s1, s2;
+        load3<T, SOA>(sig, nelem, e, s0, s1, s2);
+        T t[3][3], w[4][3], qk[4][3], iV;
+        vol[e] = hex_terms(xe, [&](int j, T vj[3]) { ld_node_half(s_xv, loc[j], 1, vj); }, s0, s1, s2, kappa, t, w,
+                           qk, iV);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            T fa[3];
+            hex_corner(i, t, w, qk, iV, fa);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) atomicAdd(s_f + a * cap + loc[i], fa[a]);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < nn; i += blockDim.x) {
+        const int64_t g = s_gid[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[SOA ? a * nnode + g : 3 * g + a] = s_f[a * cap + i];
+    }
+}
+
+// The global-colour / atomics baselines with the same compact element terms
+// (positions and velocities of the 8 corners in registers).
+template <typename T, bool SOA, bool ATOMIC>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) hex_direct_c(
+    int e0, int e1, const int32_t *__restrict__ e2n, const T *__restrict__ x, const T *__restrict__ v,
+    const T *__restrict__ sig, T *__restrict__ f, T *__restrict__ vol, int64_t nnode, int64_t nelem, T kappa)
+{
+    mp_pdl_trigger();
+    const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    const int4 *row = reinterpret_cast<const int4 *>(e2n) + 2 * (int64_t)e;
+    const int4 r0 = row[0], r1 = row[1];
+    const int nd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    T xe[8][3], ve[8][3];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        load3<T, SOA>(x, nnode, nd[i], xe[i][0], xe[i][1], xe[i][2]);
+        load3<T, SOA>(v, nnode, nd[i], ve[i][0], ve[i][1], ve[i][2]);
+    }
+    T s0, s1, s2;
+    load3<T, SOA>(sig, nelem, e, s0, s1, s2);
+    T t[3][3], w[4][3], qk[4][3], iV;
+    vol[e] = hex_terms(xe, [&](int j, T vj[3]) {
+        vj[0] = ve[j][0];
+        vj[1] = ve[j][1];
+        vj[2] = ve[j][2];
+    }, s0, s1, s2, kappa, t, w, qk, iV);
+    if (!ATOMIC) mp_pdl_wait();  // f: read-add-written by the previous colour's launch
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        T fa[3];
+        hex_corner(i, t, w, qk, iV, fa);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t j = SOA ? a * nnode + nd[i] : 3 * (int64_t)nd[i] + a;
+            if (ATOMIC)
+                atomicAdd(f + j, fa[a]);
+            else
+                f[j] += fa[a];
+        }
+    }
+}
+
 template <typename T, bool SOA>
 int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *sig, void *f, void *vol,
                     double kappa, cudaStream_t s)
@@ -366,9 +552,12 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
         // default increments: shared-memory atomics in FP32, warp-aggregated
         // ones in FP64 (whose shared-memory atomics are slower; measured)
         const int variant = mp_staged(P, sizeof(T) == 8 ? MP_STAGED_WARP_AGG : MP_STAGED_SMEM_ATOMIC);
-        auto kern = variant == MP_STAGED_SMEM_ATOMIC ? hex_hier<T, SOA, 1>
-                    : variant == MP_STAGED_WARP_AGG  ? hex_hier<T, SOA, 3>
-                                                     : hex_hier<T, SOA, 0>;
+        // shared-memory atomics with the compact element terms for blocks of
+        // at most 256 elements (the register budget of its launch bounds)
+        auto kern = variant == MP_STAGED_SMEM_ATOMIC
+                        ? (P->opts.block_size <= 256 ? hex_hier_c<T, SOA> : hex_hier<T, SOA, 1>)
+                    : variant == MP_STAGED_WARP_AGG ? hex_hier<T, SOA, 3>
+                                                    : hex_hier<T, SOA, 0>;
         int rc = mp_allow_smem(kern, smem);
         if (rc != MP_OK) return rc;
         int *err = nullptr;
@@ -399,7 +588,7 @@ int elem_assemble_t(const mp_plan *P, const void *x, const void *v, const void *
         for (int c = 0; c < P->ncolors; ++c) {
             int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
             if (e1 <= e0) continue;
-            auto kern = atomic ? hex_direct<T, SOA, true> : hex_direct<T, SOA, false>;
+            auto kern = atomic ? hex_direct_c<T, SOA, true> : hex_direct_c<T, SOA, false>;
             MP_CUDA_TRY(mp_launch(kern, (e1 - e0 + 255) / 256, 256, 0, s, overlap && !atomic, e0, e1, P->dev.map[0],
                                   (const T *)x, (const T *)v, (const T *)sig, (T *)f, (T *)vol, nnode, nelem,
                                   (T)kappa));
