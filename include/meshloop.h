@@ -120,8 +120,8 @@ typedef struct {
                             -1: default (on with MP_REORDER_PARTITION)              */
     int32_t staged;      /* MP_STAGED_* implementation of HIER loops; -1: the loop's
                             default (hex assembly, whose 3D blocks need ~10 thread
-                            colours: MP_STAGED_SMEM_ATOMIC in FP32, MP_STAGED_WARP_AGG
-                            in FP64; MP_STAGED_GATHER for res_calc in every
+                            colours: MP_STAGED_SMEM_ATOMIC in FP32 and FP64;
+                            MP_STAGED_GATHER for res_calc in every
                             arithmetic, the double-word hex assembly and adjoint,
                             and the increment-only loops; MP_STAGED_SIMPLE
                             otherwise)                                               */
