@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256, 2) hex_hier_dw(const mp_block_desc *__res
         const int64_t g0 = fpn[i0], g1 = two ? fpn[i1] : g0;
         double xv0[6], xv1[6];
         load_xv(g0, xv0);
-        load_xv(g1, xv1);
+        if (two) load_xv(g1, xv1);
         stage_node(i0, g0, xv0);
         if (two) stage_node(i1, g1, xv1);
         mp_pdl_wait();
