@@ -213,13 +213,15 @@ inline int mp_allow_smem(K kernel, int bytes)
 // ------------------------------------------------------------ 2D Euler flux
 // Per-cell primitives staged once per footprint point: velocity (u, v),
 // pressure p = (gam-1)(E - rho |u|^2 / 2) and total enthalpy density H = E + p.
+// The 1/2 of the kinetic energy is folded into gam-1 (exact scaling):
+// p = (gam-1) E - ((gam-1)/2)(ru u + rv v), one operation fewer.
 template <typename T>
 __device__ __forceinline__ void cell_prims(T rho, T ru, T rv, T E, T gm1, T &u, T &v, T &p, T &H)
 {
     T ri = T(1) / rho;
     u = ru * ri;
     v = rv * ri;
-    p = gm1 * (E - T(0.5) * (ru * u + rv * v));
+    p = gm1 * E - (T(0.5) * gm1) * (ru * u + rv * v);
     H = E + p;
 }
 
@@ -227,6 +229,9 @@ __device__ __forceinline__ void cell_prims(T rho, T ru, T rv, T E, T gm1, T &u, 
 // half normal (nxh, nyh) = n / 2:
 //   f = (F(q1).n + F(q2).n)/2 + mu (q1 - q2),  F.n = (rho V, rho u V + p n_x,
 //   rho v V + p n_y, H V),  V = u . n,  mu = eps (adt1 + adt2) / 2.
+// With W1 = V1 + mu and W2 = V2 - mu the dissipation of the first three
+// components folds into the normal velocities (rho1 V1 + mu rho1 =
+// rho1 W1, ...): 22 operations per edge instead of 26.
 template <typename T>
 __device__ __forceinline__ void edge_flux(T nxh, T nyh, T r1, T ru1, T rv1, T E1, T u1, T v1, T p1, T H1, T a1,
                                           T r2, T ru2, T rv2, T E2, T u2, T v2, T p2, T H2, T a2, T half_eps,
@@ -236,8 +241,9 @@ __device__ __forceinline__ void edge_flux(T nxh, T nyh, T r1, T ru1, T rv1, T E1
     T V2 = u2 * nxh + v2 * nyh;
     T ps = p1 + p2;
     T mu = (a1 + a2) * half_eps;
-    f[0] = r1 * V1 + r2 * V2 + mu * (r1 - r2);
-    f[1] = ru1 * V1 + ru2 * V2 + ps * nxh + mu * (ru1 - ru2);
-    f[2] = rv1 * V1 + rv2 * V2 + ps * nyh + mu * (rv1 - rv2);
+    T W1 = V1 + mu, W2 = V2 - mu;
+    f[0] = r1 * W1 + r2 * W2;
+    f[1] = ru1 * W1 + ru2 * W2 + ps * nxh;
+    f[2] = rv1 * W1 + rv2 * W2 + ps * nyh;
     f[3] = H1 * V1 + H2 * V2 + mu * (E1 - E2);
 }
