@@ -69,11 +69,13 @@ __device__ __forceinline__ void dw_cell_prims(dw R, dw RU, dw RV, dw EE, dw gm1,
 }
 
 // Edge flux from the half normal (nxh, nyh) = n/2 and both cells' states,
-// primitives and eps adt / 2 (a1, a2); each component is one compensated
-// sum of products:
-//   V = u nx/2 + v ny/2,  mu = eps (adt1 + adt2) / 2,
-//   f0 = r1 V1 + r2 V2 + mu r1 - mu r2
-//   f1 = ru1 V1 + ru2 V2 + (p1 + p2) nx/2 + mu ru1 - mu ru2   (f2 likewise)
+// primitives and eps adt / 2 (a1, a2).  With mu = eps (adt1 + adt2) / 2,
+// V = u nx/2 + v ny/2 and W1 = V1 + mu, W2 = V2 - mu (accurate double-word
+// additions: V and mu may nearly cancel), the dissipation of the first
+// three components folds into the normal velocities; each component is one
+// compensated sum of products:
+//   f0 = r1 W1 + r2 W2
+//   f1 = ru1 W1 + ru2 W2 + (p1 + p2) nx/2                    (f2 likewise)
 //   f3 = H1 V1 + H2 V2 + mu E1 - mu E2
 __device__ __forceinline__ void dw_edge_flux(dw nxh, dw nyh, dw r1, dw ru1, dw rv1, dw E1, dw a1, dw u1, dw v1,
                                              dw p1, dw H1, dw r2, dw ru2, dw rv2, dw E2, dw a2, dw u2, dw v2, dw p2,
@@ -86,23 +88,18 @@ __device__ __forceinline__ void dw_edge_flux(dw nxh, dw nyh, dw r1, dw ru1, dw r
     A = dw_dot_begin(u2, nxh);
     dw_dot_add(A, v2, nyh);
     const dw V2 = dw_dot_end(A);
-    const dw mu = dw_add_fast(a1, a2);
-    A = dw_dot_begin(r1, V1);
-    dw_dot_add(A, r2, V2);
-    dw_dot_add(A, mu, r1);
-    dw_dot_add(A, mu, dw_neg(r2));
+    const dw mu = dw_add_fast(a1, a2);  // two positive terms
+    const dw W1 = dw_add(V1, mu), W2 = dw_add(V2, dw_neg(mu));
+    A = dw_dot_begin(r1, W1);
+    dw_dot_add(A, r2, W2);
     f[0] = dw_dot_end(A);
-    A = dw_dot_begin(ru1, V1);
-    dw_dot_add(A, ru2, V2);
+    A = dw_dot_begin(ru1, W1);
+    dw_dot_add(A, ru2, W2);
     dw_dot_add(A, pp, nxh);
-    dw_dot_add(A, mu, ru1);
-    dw_dot_add(A, mu, dw_neg(ru2));
     f[1] = dw_dot_end(A);
-    A = dw_dot_begin(rv1, V1);
-    dw_dot_add(A, rv2, V2);
+    A = dw_dot_begin(rv1, W1);
+    dw_dot_add(A, rv2, W2);
     dw_dot_add(A, pp, nyh);
-    dw_dot_add(A, mu, rv1);
-    dw_dot_add(A, mu, dw_neg(rv2));
     f[2] = dw_dot_end(A);
     A = dw_dot_begin(H1, V1);
     dw_dot_add(A, H2, V2);
