@@ -498,6 +498,14 @@ int mp_check_device_status(void *stream);
  * context stay usable), which mp_check_device_status then reports.
  * Errors: MP_EINVAL (sizes), MP_ECUDA.                                  */
 int mp_grid_wait_test(int32_t nctas, int64_t wait_ns, int32_t missing, void *stream);
+/* Diagnostic of the reciprocal that the native FP64 flux kernels use for
+ * 1/(2 rho) (res_calc, Sec. 3.1.1; not in the paper): y[i] = 1/(2 x[i]) for
+ * n doubles, by one third-order Newton-Raphson step from an FP32 seed (the
+ * IEEE quotient for x whose exponent field is outside [1, 2040]).  x and y
+ * are device arrays of n doubles owned by the caller; asynchronous on
+ * `stream`.  Errors: MP_EINVAL (n < 0, or a null array with n > 0),
+ * MP_ECUDA.                                                             */
+int mp_rcp_half_test(const double *x, double *y, int64_t n, void *stream);
 /* Library version string. */
 const char *mp_version(void);
 

@@ -211,10 +211,10 @@ inline int mp_allow_smem(K kernel, int bytes)
 }
 
 // ------------------------------------------------------------ 2D Euler flux
-// Per-cell primitives staged once per footprint point: velocity (u, v),
-// pressure p = (gam-1)(E - rho |u|^2 / 2) and total enthalpy density H = E + p.
-// The 1/2 of the kinetic energy is folded into gam-1 (exact scaling):
-// p = (gam-1) E - ((gam-1)/2)(ru u + rv v), one operation fewer.
+// Per-cell primitives: velocity (u, v), pressure p = (gam-1)(E - rho |u|^2 / 2)
+// and total enthalpy density H = E + p.  The 1/2 of the kinetic energy is
+// folded into gam-1 (exact scaling): p = (gam-1) E - ((gam-1)/2)(ru u + rv v).
+// Used where the full values are needed (the far-field boundary flux).
 template <typename T>
 __device__ __forceinline__ void cell_prims(T rho, T ru, T rv, T E, T gm1, T &u, T &v, T &p, T &H)
 {
@@ -225,25 +225,79 @@ __device__ __forceinline__ void cell_prims(T rho, T ru, T rv, T E, T gm1, T &u, 
     H = E + p;
 }
 
-// Edge flux from two cells' conserved states and primitives with the
-// half normal (nxh, nyh) = n / 2:
+// 1 / (2 x).  FP32: the IEEE quotient.  FP64, whose pipe bounds the flux
+// kernels on GB300: Newton-Raphson iteration for the reciprocal from an FP32
+// seed, in its third-order form y = y0 (1 + e + e^2), e = 1 - x y0 (the
+// series of 1/(1 - e); e.g. Muller et al., Handbook of Floating-Point
+// Arithmetic, 2nd ed., Sec. 11.2 and 11.3).  The seed is rcp.approx.f32 of
+// x's significand cut to its leading 20 bits, rebuilt as a double with x's
+// negated exponent by integer operations, so no FP64 conversion is issued:
+// |e| < 2^-19, hence |e|^3 < 2^-57, below FP64 rounding, and the result is
+// the product y0h (1 + (e + e^2)) with y0h = y0 / 2, one rounding: 3 FP64
+// operations instead of an IEEE division.  x whose exponent field lies
+// outside [1, 2040] (zero, subnormal, above 2^1017, infinite, NaN) takes the
+// IEEE division, so those give the IEEE results.
+template <typename T>
+__device__ __forceinline__ T rcp_half(T x)
+{
+    return T(0.5) / x;
+}
+template <>
+__device__ __forceinline__ double rcp_half<double>(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
+    if (ex - 1u >= 2040u) return 0.5 / x;
+    // leading 20 bits of the significand as a float in [1, 2)
+    const float m = __int_as_float(0x3f800000 | ((hi & 0x000fffff) << 3));
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));  // in (1/2, 1]
+    const int rb = __float_as_int(r);
+    // r 2^(1023 - ex): exponent field (rb >> 23) - 127 + 1023 - (ex - 1023),
+    // the 23 significand bits of r split over the two words
+    const int yhi = (hi & (int)0x80000000) | (((rb >> 23) + 1919 - (int)ex) << 20) | ((rb & 0x7fffff) >> 3);
+    const int ylo = rb << 29;
+    const double y0 = __hiloint2double(yhi, ylo);
+    const double y0h = __hiloint2double(yhi - (1 << 20), ylo);  // y0 / 2: exponent - 1
+    const double e = fma(-x, y0, 1.0);
+    return fma(y0h, fma(e, e, e), y0h);
+}
+
+// Per-cell primitives with the 1/2 of the central flux average folded in:
+// uh = u / 2, vh = v / 2, ph = p / 2 and H = E + p, from ri = 1 / (2 rho) and
+// gm1h = (gam-1)/2:  ph = gm1h (E - (ru uh + rv vh)), H = E + 2 ph.  With
+// these the edge flux takes the full normal n = (dy, -dx): u . n / 2 =
+// uh . n and p n / 2 = ph n, so the nodes need no scaling.
+template <typename T>
+__device__ __forceinline__ void cell_prims_half(T rho, T ru, T rv, T E, T gm1h, T &uh, T &vh, T &ph, T &H)
+{
+    const T ri = rcp_half(rho);
+    uh = ru * ri;
+    vh = rv * ri;
+    ph = gm1h * (E - (ru * uh + rv * vh));
+    H = fma(T(2), ph, E);
+}
+
+// Edge flux from two cells' conserved states and the half primitives of
+// cell_prims_half with the full normal (nx, ny) = (y1 - y2, x2 - x1):
 //   f = (F(q1).n + F(q2).n)/2 + mu (q1 - q2),  F.n = (rho V, rho u V + p n_x,
-//   rho v V + p n_y, H V),  V = u . n,  mu = eps (adt1 + adt2) / 2.
+//   rho v V + p n_y, H V),  V = u . n,  mu = eps (adt1 + adt2) / 2,
+// evaluated with the half normal velocities V1 = uh1 . n = u1 . n / 2.
 // With W1 = V1 + mu and W2 = V2 - mu the dissipation of the first three
 // components folds into the normal velocities (rho1 V1 + mu rho1 =
 // rho1 W1, ...): 22 operations per edge instead of 26.
 template <typename T>
-__device__ __forceinline__ void edge_flux(T nxh, T nyh, T r1, T ru1, T rv1, T E1, T u1, T v1, T p1, T H1, T a1,
-                                          T r2, T ru2, T rv2, T E2, T u2, T v2, T p2, T H2, T a2, T half_eps,
+__device__ __forceinline__ void edge_flux(T nx, T ny, T r1, T ru1, T rv1, T E1, T uh1, T vh1, T ph1, T H1, T a1,
+                                          T r2, T ru2, T rv2, T E2, T uh2, T vh2, T ph2, T H2, T a2, T half_eps,
                                           T f[4])
 {
-    T V1 = u1 * nxh + v1 * nyh;
-    T V2 = u2 * nxh + v2 * nyh;
-    T ps = p1 + p2;
+    T V1 = uh1 * nx + vh1 * ny;
+    T V2 = uh2 * nx + vh2 * ny;
+    T ps = ph1 + ph2;
     T mu = (a1 + a2) * half_eps;
     T W1 = V1 + mu, W2 = V2 - mu;
     f[0] = r1 * W1 + r2 * W2;
-    f[1] = ru1 * W1 + ru2 * W2 + ps * nxh;
-    f[2] = rv1 * W1 + rv2 * W2 + ps * nyh;
+    f[1] = ru1 * W1 + ru2 * W2 + ps * nx;
+    f[2] = rv1 * W1 + rv2 * W2 + ps * ny;
     f[3] = H1 * V1 + H2 * V2 + mu * (E1 - E2);
 }

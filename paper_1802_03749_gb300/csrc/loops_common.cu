@@ -1,5 +1,6 @@
 // Plan upload, library scratch and the direct loops of the time step
 // (save_soln, update with the FP64 residual sum).
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -194,6 +195,31 @@ extern "C" int mp_grid_wait_test(int32_t nctas, int64_t wait_ns, int32_t missing
     cfg.numAttrs = 1;
     MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, grid_wait_probe, g_wait_count[dev], (unsigned)(nctas + missing),
                                    (unsigned long long)wait_ns, err));
+    return MP_OK;
+}
+
+// ------------------------------------------------- flux kernels' reciprocal
+
+namespace {
+__global__ void rcp_half_probe(const double *__restrict__ x, double *__restrict__ y, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = rcp_half(x[i]);
+}
+}  // namespace
+
+extern "C" int mp_rcp_half_test(const double *x, double *y, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return MP_EINVAL;
+    if (n == 0) return MP_OK;
+    for (const void *p : {(const void *)x, (const void *)y}) {  // device memory only
+        cudaPointerAttributes a;
+        MP_CUDA_TRY(cudaPointerGetAttributes(&a, p));
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return MP_EINVAL;
+    }
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    rcp_half_probe<<<grid, 256, 0, as_stream(stream)>>>(x, y, n);
+    MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
 

@@ -21,8 +21,9 @@ namespace {
 
 // Dynamic shared memory layout for a block with cap_c cells and cap_n nodes:
 //   T  q[4][cap_c], adt[cap_c], u[cap_c], v[cap_c], p[cap_c], H[cap_c]
+//                            (u, v, p halved: cell_prims_half)
 //   T  inc[4][cap_c]         (res prefetched at staging, increments added on)
-//   T  xh[2][cap_n]          (half coordinates, n/2 = differences of these)
+//   T  x[2][cap_n]           (node coordinates)
 //   int gid[cap_c]
 //
 // Increment forms (template INC):
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
                                                       const int32_t *__restrict__ fp, const T *__restrict__ x,
                                                       const T *__restrict__ q, const T *__restrict__ adt,
                                                       T *__restrict__ res, int64_t nnode, int64_t ncell, int cap_c,
-                                                      int cap_n, T gm1, T half_eps, int *__restrict__ err)
+                                                      int cap_n, T gm1h, T half_eps, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_q = reinterpret_cast<T *>(smem_raw);
@@ -90,8 +91,8 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
     T *s_p = s_v + cap_c;
     T *s_H = s_p + cap_c;
     T *s_inc = s_H + cap_c;
-    T *s_xh = s_inc + 4 * cap_c;
-    int *s_gid = reinterpret_cast<int *>(s_xh + 2 * cap_n);
+    T *s_x = s_inc + 4 * cap_c;
+    int *s_gid = reinterpret_cast<int *>(s_x + 2 * cap_n);
 
     mp_pdl_trigger();
     const mp_block_desc d = desc[block0 + blockIdx.x];
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
             E = (T)a.w;
         }
         T u, v, p, H;
-        cell_prims(r, ru, rv, E, gm1, u, v, p, H);
+        cell_prims_half(r, ru, rv, E, gm1h, u, v, p, H);
         s_q[i] = r;
         s_q[cap_c + i] = ru;
         s_q[2 * cap_c + i] = rv;
@@ -168,7 +169,6 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         s_inc[2 * cap_c + i] = r2;
         s_inc[3 * cap_c + i] = r3;
     };
-    // nodes as half coordinates (exact scaling by 1/2)
     auto stage_node = [&](int i) {
         int g = fpn[i];
         T px, py;
@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
             px = (T)a.x;
             py = (T)a.y;
         }
-        s_xh[i] = T(0.5) * px;
-        s_xh[cap_n + i] = T(0.5) * py;
+        s_x[i] = px;
+        s_x[cap_n + i] = py;
     };
     const int ncw = (nc + 31) & ~31, nfree = (int)blockDim.x - ncw;
     const bool split = nfree >= 32 && 2 * nfree >= nn;
@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
         const int na = l.x, nb = l.y;
         c1 = l.z;
         c2 = l.w;
-        T nxh = s_xh[cap_n + na] - s_xh[cap_n + nb];
-        T nyh = s_xh[nb] - s_xh[na];
-        edge_flux(nxh, nyh, s_q[c1], s_q[cap_c + c1], s_q[2 * cap_c + c1], s_q[3 * cap_c + c1], s_u[c1], s_v[c1],
+        T nx = s_x[cap_n + na] - s_x[cap_n + nb];
+        T ny = s_x[nb] - s_x[na];
+        edge_flux(nx, ny, s_q[c1], s_q[cap_c + c1], s_q[2 * cap_c + c1], s_q[3 * cap_c + c1], s_u[c1], s_v[c1],
                   s_p[c1], s_H[c1], s_adt[c1], s_q[c2], s_q[cap_c + c2], s_q[2 * cap_c + c2], s_q[3 * cap_c + c2],
                   s_u[c2], s_v[c2], s_p[c2], s_H[c2], s_adt[c2], half_eps, f);
     }
@@ -354,12 +354,12 @@ __device__ __forceinline__ double flip_sign(double v)
 // The gather form of the staged kernel, with every value another thread
 // reads stored as one vector record in shared memory:
 //   T  cq[cap_c][4]   rho, ru, rv, E
-//   T  cp[cap_c][4]   u, v, p, H              (per-cell primitives)
+//   T  cp[cap_c][4]   u/2, v/2, p/2, H        (cell_prims_half)
 //   T  cr[cap_c][4]   res, prefetched at staging
 //   T  f[2 S + 1][4]  FP32: the flux of every edge of the block (S =
 //                     blockDim) at [e], its negation at [S + e], zeros at
 //                     [2 S];  FP64: [S + 1][4], the fluxes (and a zero row)
-//   T  xh[cap_n][2]   half coordinates of the nodes
+//   T  x[cap_n][2]    coordinates of the nodes
 //   ushort4 ge[gw4][cap_c]  the cells' gather rows, as indices into f
 //   int gid[cap_c]
 //   T  ca[cap_c]      eps adt / 2
@@ -392,7 +392,7 @@ struct res_g_args {
     T *res;
     int64_t nnode, ncell;
     int gw4, cap_c, cap_n;
-    T gm1, half_eps;
+    T gm1h, half_eps;  // (gam-1)/2, eps/2
     int *err;
 };
 
@@ -413,7 +413,7 @@ __device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
     T *__restrict__ res = A.res;
     const int64_t nnode = A.nnode, ncell = A.ncell;
     const int gw4 = A.gw4, cap_c = A.cap_c, cap_n = A.cap_n;
-    const T gm1 = A.gm1, half_eps = A.half_eps;
+    const T gm1h = A.gm1h, half_eps = A.half_eps;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bd = blockDim.x, tid = threadIdx.x;
     const int nrow = GW1 ? 1 : gw4;
@@ -423,8 +423,8 @@ __device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
     T *s_f = s_cr + 4 * cap_c;
     constexpr bool NEG_ROWS = sizeof(T) == 4;  // negated copies of the fluxes in f
     const int nfrow = NEG_ROWS ? 2 * bd + 1 : bd + 1;
-    T *s_xh = s_f + 4 * nfrow;
-    ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_xh + 2 * cap_n);
+    T *s_x = s_f + 4 * nfrow;
+    ushort4 *s_ge = reinterpret_cast<ushort4 *>(s_x + 2 * cap_n);
     int *s_gid = reinterpret_cast<int *>(s_ge + nrow * cap_c);
     T *s_ca = reinterpret_cast<T *>(s_gid + cap_c + (sizeof(T) == 8 ? (cap_c & 1) : 0));
 
@@ -466,7 +466,7 @@ __device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
         T r0, r1, r2, r3;
         load_res<T, SOA, PERSIST>(res, ncell, g, r0, r1, r2, r3);
         T u, v, p, H;
-        cell_prims(r, ru, rv, E, gm1, u, v, p, H);
+        cell_prims_half(r, ru, rv, E, gm1h, u, v, p, H);
         st_row4(s_cq, i, r, ru, rv, E);
         st_row4(s_cp, i, u, v, p, H);
         st_row4(s_cr, i, r0, r1, r2, r3);
@@ -479,12 +479,12 @@ __device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
         if (i0 < nn) load_node<T, SOA>(x, nnode, fpn[i0], px0, py0);
         if (i1 < nn) load_node<T, SOA>(x, nnode, fpn[i1], px1, py1);
         if (i0 < nn) {
-            s_xh[2 * i0] = T(0.5) * px0;
-            s_xh[2 * i0 + 1] = T(0.5) * py0;
+            s_x[2 * i0] = px0;
+            s_x[2 * i0 + 1] = py0;
         }
         if (i1 < nn) {
-            s_xh[2 * i1] = T(0.5) * px1;
-            s_xh[2 * i1 + 1] = T(0.5) * py1;
+            s_x[2 * i1] = px1;
+            s_x[2 * i1 + 1] = py1;
         }
     };
     const int ncw = (nc + 31) & ~31, nfree = bd - ncw;
@@ -497,8 +497,8 @@ __device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
 
     if (active) {
         const int na = l.x, nb = l.y, c1 = l.z, c2 = l.w;
-        const T nxh = s_xh[2 * na + 1] - s_xh[2 * nb + 1];
-        const T nyh = s_xh[2 * nb] - s_xh[2 * na];
+        const T nx = s_x[2 * na + 1] - s_x[2 * nb + 1];
+        const T ny = s_x[2 * nb] - s_x[2 * na];
         T r1, ru1, rv1, E1, u1, v1, p1, H1, r2, ru2, rv2, E2, u2, v2, p2, H2;
         ld_row4(s_cq, c1, r1, ru1, rv1, E1);
         ld_row4(s_cp, c1, u1, v1, p1, H1);
@@ -506,7 +506,7 @@ __device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
         ld_row4(s_cp, c2, u2, v2, p2, H2);
         T f[4];
         // eps adt / 2 is folded in per cell: mu = a1 + a2
-        edge_flux(nxh, nyh, r1, ru1, rv1, E1, u1, v1, p1, H1, s_ca[c1], r2, ru2, rv2, E2, u2, v2, p2, H2, s_ca[c2],
+        edge_flux(nx, ny, r1, ru1, rv1, E1, u1, v1, p1, H1, s_ca[c1], r2, ru2, rv2, E2, u2, v2, p2, H2, s_ca[c2],
                   T(1), f);
         st_row4(s_f, tid, f[0], f[1], f[2], f[3]);
         if (NEG_ROWS) st_row4(s_f, bd + tid, flip_sign(f[0]), flip_sign(f[1]), flip_sign(f[2]), flip_sign(f[3]));
@@ -599,7 +599,7 @@ template <typename T, bool SOA, bool ATOMIC>
 __global__ void __launch_bounds__(256) res_calc_direct(int e0, int e1, const int32_t *__restrict__ e2n,
                                                        const int32_t *__restrict__ e2c, const T *__restrict__ x,
                                                        const T *__restrict__ q, const T *__restrict__ adt,
-                                                       T *__restrict__ res, int64_t nnode, int64_t ncell, T gm1,
+                                                       T *__restrict__ res, int64_t nnode, int64_t ncell, T gm1h,
                                                        T half_eps)
 {
     mp_pdl_trigger();
@@ -615,12 +615,10 @@ __global__ void __launch_bounds__(256) res_calc_direct(int e0, int e1, const int
     load_cell<T, SOA>(q, ncell, cc.y, r2, ru2, rv2, E2);
     T a1 = adt[cc.x], a2 = adt[cc.y];
     T u1, v1, p1, H1, u2, v2, p2, H2;
-    cell_prims(r1, ru1, rv1, E1, gm1, u1, v1, p1, H1);
-    cell_prims(r2, ru2, rv2, E2, gm1, u2, v2, p2, H2);
-    T nxh = T(0.5) * ya - T(0.5) * yb;
-    T nyh = T(0.5) * xb - T(0.5) * xa;
+    cell_prims_half(r1, ru1, rv1, E1, gm1h, u1, v1, p1, H1);
+    cell_prims_half(r2, ru2, rv2, E2, gm1h, u2, v2, p2, H2);
     T f[4];
-    edge_flux(nxh, nyh, r1, ru1, rv1, E1, u1, v1, p1, H1, a1, r2, ru2, rv2, E2, u2, v2, p2, H2, a2, half_eps, f);
+    edge_flux(ya - yb, xb - xa, r1, ru1, rv1, E1, u1, v1, p1, H1, a1, r2, ru2, rv2, E2, u2, v2, p2, H2, a2, half_eps, f);
     if (!ATOMIC) mp_pdl_wait();  // res: read-add-written by the previous colour's launch
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -642,7 +640,7 @@ template <typename T, bool SOA>
 __global__ void __launch_bounds__(256) res_calc_step1(int n, const int32_t *__restrict__ e2n,
                                                       const int32_t *__restrict__ e2c, const T *__restrict__ x,
                                                       const T *__restrict__ q, const T *__restrict__ adt,
-                                                      T *__restrict__ scratch, int64_t nnode, int64_t ncell, T gm1,
+                                                      T *__restrict__ scratch, int64_t nnode, int64_t ncell, T gm1h,
                                                       T half_eps)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -656,10 +654,10 @@ __global__ void __launch_bounds__(256) res_calc_step1(int n, const int32_t *__re
     load_cell<T, SOA>(q, ncell, cc.x, r1, ru1, rv1, E1);
     load_cell<T, SOA>(q, ncell, cc.y, r2, ru2, rv2, E2);
     T u1, v1, p1, H1, u2, v2, p2, H2;
-    cell_prims(r1, ru1, rv1, E1, gm1, u1, v1, p1, H1);
-    cell_prims(r2, ru2, rv2, E2, gm1, u2, v2, p2, H2);
+    cell_prims_half(r1, ru1, rv1, E1, gm1h, u1, v1, p1, H1);
+    cell_prims_half(r2, ru2, rv2, E2, gm1h, u2, v2, p2, H2);
     T f[4];
-    edge_flux(T(0.5) * ya - T(0.5) * yb, T(0.5) * xb - T(0.5) * xa, r1, ru1, rv1, E1, u1, v1, p1, H1, adt[cc.x], r2,
+    edge_flux(ya - yb, xb - xa, r1, ru1, rv1, E1, u1, v1, p1, H1, adt[cc.x], r2,
               ru2, rv2, E2, u2, v2, p2, H2, adt[cc.y], half_eps, f);
     T *o = scratch + 8 * (int64_t)e;
 #pragma unroll
@@ -760,7 +758,7 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
                cudaStream_t s)
 {
     const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
-    const T gm1 = (T)(gam - 1.0), half_eps = (T)(0.5 * eps);
+    const T gm1h = (T)(0.5 * (gam - 1.0)), half_eps = (T)(0.5 * eps);
     const int co = P->opts.coloring;
     if (co == MP_COLOR_HIER) {
         if (P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
@@ -784,7 +782,7 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
                              (sizeof(T) == 8 ? 4 : 0);
             const res_g_args<T> A{P->dev.desc, reinterpret_cast<const ushort4 *>(P->dev.lmap),
                                   reinterpret_cast<const ushort4 *>(P->dev.gat), fp, (const T *)x, (const T *)q,
-                                  (const T *)adt, (T *)res, nnode, ncell, gw4, cap_c, cap_n, gm1, half_eps, err};
+                                  (const T *)adt, (T *)res, nnode, ncell, gw4, cap_c, cap_n, gm1h, half_eps, err};
             if (variant == MP_STAGED_PERSISTENT) {
                 auto kern = gw1 ? res_calc_hier_gp<T, SOA, true> : res_calc_hier_gp<T, SOA, false>;
                 if ((rc = mp_allow_smem(kern, smem)) != MP_OK) return rc;
@@ -830,7 +828,7 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
             if (nb == 0) continue;
             MP_CUDA_TRY(mp_launch(kern, nb, bs, smem, s, overlap, P->dev.desc, b0,
                                   reinterpret_cast<const ushort4 *>(P->dev.lmap), P->dev.tcolor, fp, (const T *)x,
-                                  (const T *)q, (const T *)adt, (T *)res, nnode, ncell, cap_c, cap_n, gm1, half_eps,
+                                  (const T *)q, (const T *)adt, (T *)res, nnode, ncell, cap_c, cap_n, gm1h, half_eps,
                                   err));
             overlap = true;
         }
@@ -841,7 +839,7 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
         const int n = (int)P->from_size;
         res_calc_step1<T, SOA><<<(n + 255) / 256, 256, 0, s>>>(n, P->dev.map[0], P->dev.map[1], (const T *)x,
                                                                 (const T *)q, (const T *)adt, (T *)scratch, nnode,
-                                                                ncell, gm1, half_eps);
+                                                                ncell, gm1h, half_eps);
         MP_CUDA_TRY(cudaGetLastError());
         return mp_twostep_gather(P, sizeof(T) == 8 ? MP_F64 : MP_F32, 4, scratch, res, s);
     } else {
@@ -853,7 +851,7 @@ int res_calc_t(const mp_plan *P, const void *x, const void *q, const void *adt, 
             int grid = (e1 - e0 + 255) / 256;
             auto kern = atomic ? res_calc_direct<T, SOA, true> : res_calc_direct<T, SOA, false>;
             MP_CUDA_TRY(mp_launch(kern, grid, 256, 0, s, overlap && !atomic, e0, e1, P->dev.map[0], P->dev.map[1],
-                                  (const T *)x, (const T *)q, (const T *)adt, (T *)res, nnode, ncell, gm1,
+                                  (const T *)x, (const T *)q, (const T *)adt, (T *)res, nnode, ncell, gm1h,
                                   half_eps));
             overlap = true;
         }

@@ -130,7 +130,7 @@ __device__ __forceinline__ void issue_data(const mp_block_desc &d, const pipe_la
 // Native arithmetic (E = T = float or double).
 template <typename T>
 struct native_ops {
-    static constexpr int work_bytes = 4 * sizeof(T);  // u, v, p, H per cell
+    static constexpr int work_bytes = 4 * sizeof(T);  // u/2, v/2, p/2, H per cell (cell_prims_half)
 };
 
 template <typename T, bool SOA>
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(512) res_calc_pipe(const mp_block_desc *__rest
                                                      const int32_t *__restrict__ fp, const T *__restrict__ x,
                                                      const T *__restrict__ q, const T *__restrict__ adt,
                                                      T *__restrict__ res, int64_t nnode, int64_t ncell,
-                                                     pipe_layout L, T gm1, T half_eps, int *__restrict__ err)
+                                                     pipe_layout L, T gm1h, T half_eps, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(512) res_calc_pipe(const mp_block_desc *__rest
     auto stage = [&](int k) { return sm + (k & 1) * L.stage_bytes(); };
     auto ids_c = [&](int k) { return reinterpret_cast<int *>(sm + L.ids_off(k % 3)); };
     auto ids_n = [&](int k) { return reinterpret_cast<int *>(sm + L.ids_off(k % 3) + align16(L.cap_c * 4)); };
-    T *work = reinterpret_cast<T *>(sm + L.work_off());  // [cap_c][4]: u, v, p, H
+    T *work = reinterpret_cast<T *>(sm + L.work_off());  // [cap_c][4]: u/2, v/2, p/2, H
 
     // prologue: ids of block 0, then its data and the ids of block 1
     issue_ids(sd[0], fp, ids_c(0), ids_n(0));
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(512) res_calc_pipe(const mp_block_desc *__rest
         // per-cell primitives
         for (int i = tid; i < d.fp_count[1]; i += blockDim.x) {
             T u, v, p, H;
-            cell_prims(sq[4 * i], sq[4 * i + 1], sq[4 * i + 2], sq[4 * i + 3], gm1, u, v, p, H);
+            cell_prims_half(sq[4 * i], sq[4 * i + 1], sq[4 * i + 2], sq[4 * i + 3], gm1h, u, v, p, H);
             work[4 * i] = u;
             work[4 * i + 1] = v;
             work[4 * i + 2] = p;
@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(512) res_calc_pipe(const mp_block_desc *__rest
             c1 = lw.y & 0xffff;
             c2 = lw.y >> 16;
             my_color = stc[tid];
-            const T nxh = T(0.5) * sx[2 * na + 1] - T(0.5) * sx[2 * nb_ + 1];
-            const T nyh = T(0.5) * sx[2 * nb_] - T(0.5) * sx[2 * na];
-            edge_flux(nxh, nyh, sq[4 * c1], sq[4 * c1 + 1], sq[4 * c1 + 2], sq[4 * c1 + 3], work[4 * c1],
+            const T nx = sx[2 * na + 1] - sx[2 * nb_ + 1];
+            const T ny = sx[2 * nb_] - sx[2 * na];
+            edge_flux(nx, ny, sq[4 * c1], sq[4 * c1 + 1], sq[4 * c1 + 2], sq[4 * c1 + 3], work[4 * c1],
                       work[4 * c1 + 1], work[4 * c1 + 2], work[4 * c1 + 3], sa[c1], sq[4 * c2], sq[4 * c2 + 1],
                       sq[4 * c2 + 2], sq[4 * c2 + 3], work[4 * c2], work[4 * c2 + 1], work[4 * c2 + 2],
                       work[4 * c2 + 3], sa[c2], half_eps, f);
@@ -279,7 +279,7 @@ int res_calc_pipe_t(const mp_plan *P, const void *x, const void *q, const void *
         kern<<<grid, P->opts.block_size, smem, s>>>(P->dev.desc, b0, nb, reinterpret_cast<const uint2 *>(P->dev.lmap),
                                                     P->dev.tcolor, P->dev.fp, (const T *)x, (const T *)q,
                                                     (const T *)adt, (T *)res, P->maps[0].to_size, P->maps[1].to_size,
-                                                    L, (T)(gam - 1.0), (T)(0.5 * eps), err);
+                                                    L, (T)(0.5 * (gam - 1.0)), (T)(0.5 * eps), err);
     }
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;

@@ -155,6 +155,28 @@ def test_res_calc_double_word_scaled_inputs(ml, xs, qs):
         assert rel_l2(got, ref) <= 1e-12, (coloring, staged)
 
 
+@pytest.mark.parametrize("xs,qs", [(1e-100, 1.0), (1e100, 1.0), (1.0, 1e150), (1.0, 1e-150), (1e-50, 1e-140),
+                                   (1e50, 1e140)])
+def test_res_calc_fp64_scaled_inputs(ml, xs, qs):
+    """Native FP64 on inputs scaled far from the unit free stream (the
+    reciprocal 1/(2 rho) of the flux kernels at densities from 1e-150 to
+    1e150): every strategy stays within the FP64 bar.  States above about
+    1e154 would overflow the oracle's own |rho u|^2."""
+    m0, q0, _ = case(60, 30)
+    import copy
+    m = copy.copy(m0)
+    m.x = m0.x * xs
+    q = q0 * qs
+    adt = oracle.adt_calc(m.cell2node, m.x, q)
+    ref = oracle.res_calc(m.edge2node, m.edge2cell, m.x, q, adt)
+    for coloring, staged in (("hier", None), ("hier", "simple"), ("hier", "pipelined"), ("global", None),
+                             ("atomic", None)):
+        got, _ = run_res_calc(ml, m, q, adt, coloring, "partition" if coloring == "hier" else "rcm", "aos", "f64",
+                              block_size=256, staged=staged)
+        s = np.abs(ref).max()                 # the norm's squares would overflow at 1e186
+        assert np.all(np.isfinite(got)) and rel_l2(got / s, ref / s) <= 1e-12, (coloring, staged)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("compute", ["f64", "f64_colour", "dw", "dw_colour", "dw_global", "dw_atomic", "f32"])
 def test_res_calc_full_size_parity(ml, compute):
