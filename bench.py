@@ -68,7 +68,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic records: one text file per configuration under profiles/,
 # written by --record-traffic from an ncu CSV of the headline kernel
-TRAFFIC_SOURCES = ("loops_res.cu", "loops_res_dw.cu", "dw.cuh", "common.cuh", "plan_internal.h", "plan.cpp")
+TRAFFIC_SOURCES = ("loops_res.cu", "loops_res_dw.cu", "rows.cuh", "dw.cuh", "common.cuh", "plan_internal.h",
+                   "plan.cpp")
 HEAD_KERNEL = {"f64": "res_calc_hier_g", "f32": "res_calc_hier_g", "dw": "res_calc_hier_dw"}
 
 
@@ -676,6 +677,9 @@ def bench_shapes(ml, torch, timer, args):
     return rows
 
 
+ADJ_BLOCK = 320  # native adjoint, gather form (fastest of 128-512)
+
+
 def bench_adjoint(ml, torch, timer, args):
     from paper_1802_03749_gb300.mesh import AirfoilPlans
     hbm, _ = read_peaks()
@@ -685,11 +689,13 @@ def bench_adjoint(ml, torch, timer, args):
     aq = meshgen.quad_state(am.ncell)
     aadt = synthetic_adt(am)
     rb = meshgen.adjoint_seed(am.ncell)
-    for coloring, reorder, comp, staged in (("hier", "partition", None, None), ("hier", "partition", "dw", "gather"),
-                                            ("hier", "partition", "dw", "simple"), ("atomic", "rcm", None, None)):
+    for coloring, reorder, comp, staged, bs in (("hier", "partition", None, "gather", ADJ_BLOCK),
+                                                ("hier", "partition", None, "simple", 384),
+                                                ("hier", "partition", "dw", "gather", 256),
+                                                ("hier", "partition", "dw", "simple", 256),
+                                                ("atomic", "rcm", None, None, 256), ("global", "rcm", None, None, 256)):
         P = AirfoilPlans(am.ncell, am.nnode, am.edge2node, am.edge2cell, am.bedge2node, am.bedge2cell, am.cell2node,
-                         block_size=256 if comp else 384, reorder=reorder, coloring=coloring, adjoint=True,
-                         staged=staged)
+                         block_size=bs, reorder=reorder, coloring=coloring, adjoint=True, staged=staged)
         P.res.upload()
         t = lambda a, w: torch.tensor(P.to_plan(a, w), device="cuda")
         x, qd, ad, rbd = t(am.x, "node"), t(aq, "cell"), t(aadt, "cell"), t(rb, "cell")

@@ -310,7 +310,7 @@ int loop_res_calc_host(const mp_plan *plan, int32_t dtype, const void *x, const 
  *  MP_STAGED_SMEM_ATOMIC: as SIMPLE, but increments go to shared memory with
  *    atomic adds instead of one pass per thread colour (one barrier; the
  *    order of additions, and so the rounding, is not fixed).  Not for the
- *    double-word res_calc or the adjoint, which run SIMPLE.
+ *    double-word res_calc or the adjoint, which run SIMPLE instead.
  * Block colouring orders the write-back in every variant.                */
 enum { MP_STAGED_SIMPLE = 1, MP_STAGED_PIPELINED = 0, MP_STAGED_SMEM_ATOMIC = 2, MP_STAGED_GATHER = 3,
        MP_STAGED_INC_ONLY = 4, MP_STAGED_INC_ONLY_GATHER = 5, MP_STAGED_WARP_AGG = 6,
@@ -414,7 +414,10 @@ int loop_elem_assemble(const mp_plan *plan, int32_t dtype, const void *x, const 
 /* Adjoint of res_calc with x, q, adt fixed (adt not differentiated):
  *   q_bar += (d res/d q)^T res_bar,  x_bar += (d res/d x)^T res_bar.
  * Both maps are written, so the plan has maps {edge->node (2, written),
- * edge->cell (2, written)}.  dtype MP_F64, MP_F32 or MP_F64_DW.         */
+ * edge->cell (2, written)}.  dtype MP_F64, MP_F32 or MP_F64_DW.  HIER
+ * plans sum each cell's and node's increments through the gather rows by
+ * default (a fixed order, deterministic; MP_STAGED_SIMPLE for thread
+ * colours); GLOBAL and ATOMIC as loop_res_calc.                         */
 int loop_adjoint(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                  const void *res_bar, void *q_bar, void *x_bar, double gam, double eps,
                  void *stream);
@@ -498,14 +501,15 @@ int mp_check_device_status(void *stream);
  * context stay usable), which mp_check_device_status then reports.
  * Errors: MP_EINVAL (sizes), MP_ECUDA.                                  */
 int mp_grid_wait_test(int32_t nctas, int64_t wait_ns, int32_t missing, void *stream);
-/* Diagnostic of the reciprocal that the native FP64 flux kernels use for
- * 1/(2 rho) (res_calc, Sec. 3.1.1; not in the paper): y[i] = 1/(2 x[i]) for
- * n doubles, by one third-order Newton-Raphson step from an FP32 seed (the
- * IEEE quotient for x whose exponent field is outside [1, 2040]).  x and y
- * are device arrays of n doubles owned by the caller; asynchronous on
- * `stream`.  Errors: MP_EINVAL (n < 0, or a null array with n > 0),
- * MP_ECUDA.                                                             */
-int mp_rcp_half_test(const double *x, double *y, int64_t n, void *stream);
+/* Diagnostic of the FP64 helpers of the native flux kernels (res_calc,
+ * Sec. 3.1.1, and its adjoint); not in the paper.  For n doubles, mode 0:
+ * y = 1/x and mode 1: y = 1/(2 x), by one third-order Newton-Raphson step
+ * from an FP32 seed (the IEEE quotient for x whose exponent field is
+ * outside [1, 2040]); mode 2: y = x/2 by an exponent decrement (exact; x *
+ * 0.5 where that is not exact).  x and y are device arrays of n doubles
+ * owned by the caller; asynchronous on `stream`.  Errors: MP_EINVAL (n < 0,
+ * a null or host array with n > 0, mode not 0..2), MP_ECUDA.            */
+int mp_recip_test(const double *x, double *y, int64_t n, int32_t mode, void *stream);
 /* Library version string. */
 const char *mp_version(void);
 

@@ -25,7 +25,7 @@ __all__ = [
     "MeshLoopError", "Plan", "lib", "loop_res_calc", "loop_bres_calc", "loop_adt_calc", "loop_save_soln",
     "loop_res_calc_host", "loop_update", "loop_update_noalloc", "loop_elem_assemble", "loop_adjoint",
     "loop_space_disc", "loop_getacc", "loop_face_flux", "mesh_map_renumber", "mp_check_device_status",
-    "mp_grid_wait_test", "mp_rcp_half_test",
+    "mp_grid_wait_test", "mp_recip_test",
     "REORDER", "COLORING", "LAYOUT", "MP_MAX_BLOCK_COLORS",
 ]
 
@@ -116,7 +116,7 @@ SIGNATURES = {
     "mp_error_string": (ctypes.c_char_p, [_I32]),
     "mp_check_device_status": (_I32, [_P]),
     "mp_grid_wait_test": (_I32, [_I32, _I64, _I32, _P]),
-    "mp_rcp_half_test": (_I32, [_P, _P, _I64, _P]),
+    "mp_recip_test": (_I32, [_P, _P, _I64, _I32, _P]),
     "mp_version": (ctypes.c_char_p, []),
 }
 
@@ -444,11 +444,12 @@ def mp_grid_wait_test(nctas: int, wait_ns: int, missing: int = 0, stream=None):
     _check(lib().mp_grid_wait_test(int(nctas), int(wait_ns), int(missing), _stream(stream)), "mp_grid_wait_test")
 
 
-def mp_rcp_half_test(x, y, stream=None):
-    """1/(2 x) by the native FP64 flux kernels' reciprocal
-    (``mp_rcp_half_test``): x, y contiguous float64 CUDA tensors."""
+def mp_recip_test(x, y, mode: int = 0, stream=None):
+    """The native FP64 flux kernels' helpers (``mp_recip_test``): mode 0
+    y = 1/x, 1 y = 1/(2 x), 2 y = x/2; x, y contiguous float64 CUDA
+    tensors."""
     if x.dtype != y.dtype or x.numel() != y.numel() or not (x.is_contiguous() and y.is_contiguous()):
         raise MeshLoopError(-1, "x and y: contiguous tensors of one dtype and size")
     if str(x.dtype) != "torch.float64" or not (x.is_cuda and y.is_cuda):
         raise MeshLoopError(-1, "float64 CUDA tensors expected")
-    _check(lib().mp_rcp_half_test(_ptr(x), _ptr(y), int(x.numel()), _stream(stream)), "mp_rcp_half_test")
+    _check(lib().mp_recip_test(_ptr(x), _ptr(y), int(x.numel()), int(mode), _stream(stream)), "mp_recip_test")

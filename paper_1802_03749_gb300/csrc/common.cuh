@@ -225,29 +225,25 @@ __device__ __forceinline__ void cell_prims(T rho, T ru, T rv, T E, T gm1, T &u, 
     H = E + p;
 }
 
-// 1 / (2 x).  FP32: the IEEE quotient.  FP64, whose pipe bounds the flux
-// kernels on GB300: Newton-Raphson iteration for the reciprocal from an FP32
-// seed, in its third-order form y = y0 (1 + e + e^2), e = 1 - x y0 (the
-// series of 1/(1 - e); e.g. Muller et al., Handbook of Floating-Point
-// Arithmetic, 2nd ed., Sec. 11.2 and 11.3).  The seed is rcp.approx.f32 of
-// x's significand cut to its leading 20 bits, rebuilt as a double with x's
-// negated exponent by integer operations, so no FP64 conversion is issued:
-// |e| < 2^-19, hence |e|^3 < 2^-57, below FP64 rounding, and the result is
-// the product y0h (1 + (e + e^2)) with y0h = y0 / 2, one rounding: 3 FP64
+// Reciprocals of the flux kernels, rcp(x) = 1 / x and rcp_half(x) = 1 / (2 x).
+// FP32: the IEEE quotients.  FP64, whose pipe bounds the flux kernels on
+// GB300: Newton-Raphson iteration for the reciprocal from an FP32 seed, in
+// its third-order form y = y0 (1 + e + e^2), e = 1 - x y0 (the series of
+// 1/(1 - e); e.g. Muller et al., Handbook of Floating-Point Arithmetic, 2nd
+// ed., Sec. 11.2 and 11.3).  The seed is rcp.approx.f32 of x's significand
+// cut to its leading 20 bits, rebuilt as a double with x's negated exponent
+// by integer operations, so no FP64 conversion is issued: |e| < 2^-19, hence
+// |e|^3 < 2^-57, below FP64 rounding, and the result is the product
+// y0 (1 + (e + e^2)) (or y0 / 2 times it) with one rounding: 3 FP64
 // operations instead of an IEEE division.  x whose exponent field lies
 // outside [1, 2040] (zero, subnormal, above 2^1017, infinite, NaN) takes the
 // IEEE division, so those give the IEEE results.
-template <typename T>
-__device__ __forceinline__ T rcp_half(T x)
-{
-    return T(0.5) / x;
-}
-template <>
-__device__ __forceinline__ double rcp_half<double>(double x)
+// The seed y0 of 1/x and y0/2; false when x is outside the seed's range.
+__device__ __forceinline__ bool rcp_seed(double x, double &y0, double &y0h)
 {
     const int hi = __double2hiint(x);
     const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
-    if (ex - 1u >= 2040u) return 0.5 / x;
+    if (ex - 1u >= 2040u) return false;
     // leading 20 bits of the significand as a float in [1, 2)
     const float m = __int_as_float(0x3f800000 | ((hi & 0x000fffff) << 3));
     float r;
@@ -257,10 +253,51 @@ __device__ __forceinline__ double rcp_half<double>(double x)
     // the 23 significand bits of r split over the two words
     const int yhi = (hi & (int)0x80000000) | (((rb >> 23) + 1919 - (int)ex) << 20) | ((rb & 0x7fffff) >> 3);
     const int ylo = rb << 29;
-    const double y0 = __hiloint2double(yhi, ylo);
-    const double y0h = __hiloint2double(yhi - (1 << 20), ylo);  // y0 / 2: exponent - 1
+    y0 = __hiloint2double(yhi, ylo);
+    y0h = __hiloint2double(yhi - (1 << 20), ylo);  // y0 / 2: exponent - 1
+    return true;
+}
+template <typename T>
+__device__ __forceinline__ T rcp_half(T x)
+{
+    return T(0.5) / x;
+}
+template <>
+__device__ __forceinline__ double rcp_half<double>(double x)
+{
+    double y0, y0h;
+    if (!rcp_seed(x, y0, y0h)) return 0.5 / x;
     const double e = fma(-x, y0, 1.0);
     return fma(y0h, fma(e, e, e), y0h);
+}
+template <typename T>
+__device__ __forceinline__ T rcp(T x)
+{
+    return T(1) / x;
+}
+template <>
+__device__ __forceinline__ double rcp<double>(double x)
+{
+    double y0, y0h;
+    if (!rcp_seed(x, y0, y0h)) return 1.0 / x;
+    const double e = fma(-x, y0, 1.0);
+    return fma(y0, fma(e, e, e), y0);
+}
+
+// x / 2, exact.  FP64: by decrementing the exponent field when x is normal
+// with exponent field at least 2 (integer operations, off the FP64 pipe),
+// else (zero, smallest normals, subnormals, infinities, NaN) x * 0.5.
+template <typename T>
+__device__ __forceinline__ T half_of(T x)
+{
+    return T(0.5) * x;
+}
+template <>
+__device__ __forceinline__ double half_of<double>(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
+    return ex - 2u < 2045u ? __hiloint2double(hi - (1 << 20), __double2loint(x)) : 0.5 * x;
 }
 
 // Per-cell primitives with the 1/2 of the central flux average folded in:

@@ -198,19 +198,19 @@ extern "C" int mp_grid_wait_test(int32_t nctas, int64_t wait_ns, int32_t missing
     return MP_OK;
 }
 
-// ------------------------------------------------- flux kernels' reciprocal
+// ------------------------------------------------ flux kernels' reciprocals
 
 namespace {
-__global__ void rcp_half_probe(const double *__restrict__ x, double *__restrict__ y, int64_t n)
+__global__ void recip_probe(const double *__restrict__ x, double *__restrict__ y, int64_t n, int mode)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = rcp_half(x[i]);
+        y[i] = mode == 0 ? rcp(x[i]) : mode == 1 ? rcp_half(x[i]) : half_of(x[i]);
 }
 }  // namespace
 
-extern "C" int mp_rcp_half_test(const double *x, double *y, int64_t n, void *stream)
+extern "C" int mp_recip_test(const double *x, double *y, int64_t n, int32_t mode, void *stream)
 {
-    if (n < 0 || (n > 0 && (!x || !y))) return MP_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !y)) || mode < 0 || mode > 2) return MP_EINVAL;
     if (n == 0) return MP_OK;
     for (const void *p : {(const void *)x, (const void *)y}) {  // device memory only
         cudaPointerAttributes a;
@@ -218,7 +218,7 @@ extern "C" int mp_rcp_half_test(const double *x, double *y, int64_t n, void *str
         if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return MP_EINVAL;
     }
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    rcp_half_probe<<<grid, 256, 0, as_stream(stream)>>>(x, y, n);
+    recip_probe<<<grid, 256, 0, as_stream(stream)>>>(x, y, n, mode);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

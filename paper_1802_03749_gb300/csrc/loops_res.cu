@@ -14,6 +14,7 @@
 //          two nodes from global memory and read-add-writes res directly.
 //   ATOMIC one launch; increments with FP64/FP32 atomicAdd.
 #include "common.cuh"
+#include "rows.cuh"
 
 namespace {
 
@@ -269,87 +270,6 @@ __global__ void __launch_bounds__(1024) res_calc_hier(const mp_block_desc *__res
 }
 
 // ------------------------------------------------------- GLOBAL / ATOMIC
-
-template <typename T, bool SOA>
-__device__ __forceinline__ void load_cell(const T *__restrict__ q, int64_t ncell, int g, T &r, T &ru, T &rv, T &E)
-{
-    if (SOA) {
-        r = q[g];
-        ru = q[ncell + g];
-        rv = q[2 * ncell + g];
-        E = q[3 * ncell + g];
-    } else if (sizeof(T) == 8) {
-        const double2 *q2 = reinterpret_cast<const double2 *>(q) + 2 * (int64_t)g;
-        double2 a = q2[0], b = q2[1];
-        r = (T)a.x;
-        ru = (T)a.y;
-        rv = (T)b.x;
-        E = (T)b.y;
-    } else {
-        float4 a = reinterpret_cast<const float4 *>(q)[g];
-        r = (T)a.x;
-        ru = (T)a.y;
-        rv = (T)a.z;
-        E = (T)a.w;
-    }
-}
-
-template <typename T, bool SOA>
-__device__ __forceinline__ void load_node(const T *__restrict__ x, int64_t nnode, int g, T &px, T &py)
-{
-    if (SOA) {
-        px = x[g];
-        py = x[nnode + g];
-    } else if (sizeof(T) == 8) {
-        double2 a = reinterpret_cast<const double2 *>(x)[g];
-        px = (T)a.x;
-        py = (T)a.y;
-    } else {
-        float2 a = reinterpret_cast<const float2 *>(x)[g];
-        px = (T)a.x;
-        py = (T)a.y;
-    }
-}
-
-// Rows of 4 values in shared memory, one vector access each (16-byte
-// aligned: float4, or two double2).
-template <typename T>
-__device__ __forceinline__ void st_row4(T *base, int i, T a, T b, T c, T d)
-{
-    if (sizeof(T) == 8) {
-        double2 *p = reinterpret_cast<double2 *>(base) + 2 * i;
-        p[0] = make_double2((double)a, (double)b);
-        p[1] = make_double2((double)c, (double)d);
-    } else {
-        reinterpret_cast<float4 *>(base)[i] = make_float4((float)a, (float)b, (float)c, (float)d);
-    }
-}
-template <typename T>
-__device__ __forceinline__ void ld_row4(const T *base, int i, T &a, T &b, T &c, T &d)
-{
-    if (sizeof(T) == 8) {
-        const double2 *p = reinterpret_cast<const double2 *>(base) + 2 * i;
-        const double2 u = p[0], w = p[1];
-        a = (T)u.x;
-        b = (T)u.y;
-        c = (T)w.x;
-        d = (T)w.y;
-    } else {
-        const float4 u = reinterpret_cast<const float4 *>(base)[i];
-        a = (T)u.x;
-        b = (T)u.y;
-        c = (T)u.z;
-        d = (T)u.w;
-    }
-}
-
-// -v by flipping the sign bit: an integer operation, so FP64 negations
-// do not occupy the FP64 pipe
-__device__ __forceinline__ float flip_sign(float v) { return __int_as_float(__float_as_int(v) ^ (int)0x80000000); }
-__device__ __forceinline__ double flip_sign(double v)
-{
-    return __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v));
-}
 
 // The gather form of the staged kernel, with every value another thread
 // reads stored as one vector record in shared memory:
