@@ -451,12 +451,20 @@ __device__ __forceinline__ bool res_block_g(const res_g_args<T> &A, int b)
                 } else {  // raw entry: +f, -f, or padding (0 times row 0)
                     const unsigned e = es[j];
                     const bool valid = e != 0xFFFFu;
-                    const T sg = !valid ? T(0) : ((e & 15u) == 3u ? T(-1) : T(1));
-                    ld_row4(s_f, valid ? (int)(e >> 4) : 0, v0, v1, v2, v3);
-                    a0 += sg * v0;
-                    a1 += sg * v1;
-                    a2 += sg * v2;
-                    a3 += sg * v3;
+                    // entries ascend, padding last, and the data-point order
+                    // puts a block's halo cells (fewer in-block edges) after
+                    // its interior cells: warps of halo cells skip their
+                    // trailing padding entries as a whole (FP64 only: in the
+                    // issue-bound FP32 and double-word sums the vote costs
+                    // more than the skipped additions)
+                    if (__any_sync(__activemask(), valid)) {
+                        const T sg = !valid ? T(0) : ((e & 15u) == 3u ? T(-1) : T(1));
+                        ld_row4(s_f, valid ? (int)(e >> 4) : 0, v0, v1, v2, v3);
+                        a0 += sg * v0;
+                        a1 += sg * v1;
+                        a2 += sg * v2;
+                        a3 += sg * v3;
+                    }
                 }
             }
         }
