@@ -53,8 +53,8 @@ __device__ __forceinline__ void flux_rev(T r, T ru, T rv, T u, T v, T p, T H, T 
     }
 }
 
-// smem per cell: q[4], adt, u, v, p, H, ri, rb[4], inc[4] (18 T) + gid;
-// per node: x[2], inc[2] (4 T) + gid
+// Thread-coloured kernel (Algorithm 1), smem per cell: q[4], adt, u, v, p,
+// H, ri, rb[4], inc[4] (18 T) + gid; per node: x[2], inc[2] (4 T) + gid
 template <typename T>
 __host__ __device__ constexpr int adj_smem_per_cell()
 {
