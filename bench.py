@@ -693,7 +693,8 @@ def bench_adjoint(ml, torch, timer, args):
                                                 ("hier", "partition", None, "simple", 384),
                                                 ("hier", "partition", "dw", "gather", 256),
                                                 ("hier", "partition", "dw", "simple", 256),
-                                                ("atomic", "rcm", None, None, 256), ("global", "rcm", None, None, 256)):
+                                                ("atomic", "rcm", None, None, 256), ("global", "rcm", None, None, 256),
+                                                ("atomic", "rcm", "dw", None, 256), ("global", "rcm", "dw", None, 256)):
         P = AirfoilPlans(am.ncell, am.nnode, am.edge2node, am.edge2cell, am.bedge2node, am.bedge2cell, am.cell2node,
                          block_size=bs, reorder=reorder, coloring=coloring, adjoint=True, staged=staged)
         P.res.upload()

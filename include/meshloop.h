@@ -91,9 +91,10 @@ enum { MP_F64 = 0, MP_F32 = 1, MP_F64_DW = 2 };
  * loop_res_calc, loop_adjoint, loop_elem_assemble and loop_face_flux with
  * HIER plans (res_calc and hex assembly: gather increments by default,
  * MP_STAGED_SIMPLE for thread colours; hex: blocks of at most 256 threads;
- * face flux: at most 128), and by loop_res_calc and loop_elem_assemble with
- * GLOBAL and ATOMIC plans (the Sec. 2.1 baselines in the same arithmetic:
- * FP64 read-add-write of res / f per colour, or FP64 atomicAdd).          */
+ * face flux: at most 128), and by loop_res_calc, loop_adjoint and
+ * loop_elem_assemble with GLOBAL and ATOMIC plans (the Sec. 2.1 baselines
+ * in the same arithmetic: FP64 read-add-write of the incremented data per
+ * colour, or FP64 atomicAdd).                                            */
 
 /* One map of the loop: from the loop's iteration set (set id 0) to the
  * caller's set `to_set` (ids >= 1; maps with the same id share a to-set).
@@ -417,7 +418,7 @@ int loop_elem_assemble(const mp_plan *plan, int32_t dtype, const void *x, const 
  * edge->cell (2, written)}.  dtype MP_F64, MP_F32 or MP_F64_DW.  HIER
  * plans sum each cell's and node's increments through the gather rows by
  * default (a fixed order, deterministic; MP_STAGED_SIMPLE for thread
- * colours); GLOBAL and ATOMIC as loop_res_calc.                         */
+ * colours); GLOBAL and ATOMIC as loop_res_calc, in every dtype.         */
 int loop_adjoint(const mp_plan *plan, int32_t dtype, const void *x, const void *q, const void *adt,
                  const void *res_bar, void *q_bar, void *x_bar, double gam, double eps,
                  void *stream);

@@ -396,7 +396,8 @@ def loop_elem_assemble(plan: Plan, x, v, sig, f, vol, kappa: float = 0.01, strea
 
 def loop_adjoint(plan: Plan, x, q, adt, res_bar, q_bar, x_bar, gam: float = 1.4, eps: float = 0.05,
                  stream=None, compute: str | None = None):
-    """``compute="dw"`` selects double-word arithmetic on FP64 data (HIER plans)."""
+    """``compute="dw"`` selects double-word arithmetic on FP64 data (HIER,
+    GLOBAL and ATOMIC plans)."""
     dt = _dtype_of(x, q, adt, res_bar, q_bar, x_bar)
     if compute == "dw":
         if dt != DTYPE["f64"]:

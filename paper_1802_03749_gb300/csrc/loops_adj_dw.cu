@@ -37,12 +37,24 @@ __device__ __forceinline__ void stw(float2 *a, int i, dw v) { a[i] = make_float2
 constexpr int kAdjDwCellBytes = 32 + 80 + 64 + 4;
 constexpr int kAdjDwNodeBytes = 32 + 16 + 4;
 
-// One side's reverse sweep; accumulates n_b.
-__device__ __forceinline__ void flux_rev_dw(const float2 *const S[10], int c, dw nx, dw ny, const dw h[4], dw gm1,
-                                            dw qb[4], dw_acc &nbx, dw_acc &nby, bool first)
+// Per-cell values of the reverse sweep from q = (rho, ru, rv, E): H = E + p,
+// 1/rho, u, v, p and K = |u|^2 / 2.
+__device__ __forceinline__ void dw_adj_prims(const dw qq[4], dw gm1, dw &H, dw &ri, dw &u, dw &v, dw &p, dw &K)
 {
-    const dw r = ldw(S[0], c), ru = ldw(S[1], c), rv = ldw(S[2], c), H = ldw(S[3], c), ri = ldw(S[4], c);
-    const dw u = ldw(S[5], c), v = ldw(S[6], c), p = ldw(S[7], c), K = ldw(S[8], c);
+    ri = dw_recip(qq[0]);
+    u = dw_mul(qq[1], ri);
+    v = dw_mul(qq[2], ri);
+    dw_acc A = dw_dot_begin(u, u);
+    dw_dot_add(A, v, v);
+    K = dw_scale2(dw_dot_end(A), 0.5f);
+    p = dw_mul(gm1, dw_sub(qq[3], dw_mul(qq[0], K)));
+    H = dw_add(qq[3], p);
+}
+
+// One side's reverse sweep; accumulates n_b.
+__device__ __forceinline__ void flux_rev_dw(dw r, dw ru, dw rv, dw H, dw ri, dw u, dw v, dw p, dw K, dw nx, dw ny,
+                                            const dw h[4], dw gm1, dw qb[4], dw_acc &nbx, dw_acc &nby, bool first)
+{
     dw_acc A = dw_dot_begin(u, nx);
     dw_dot_add(A, v, ny);
     const dw V = dw_dot_end(A);
@@ -144,17 +156,13 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
         mp_pdl_wait();  // q_bar, x_bar: written by the previous colour's launch
 #pragma unroll
         for (int k = 0; k < 4; ++k) s_qb[k * cap_c + i] = qbar[SOA ? k * ncell + g : 4 * g + k];
-        const dw ri = dw_recip(qq[0]);
-        const dw u = dw_mul(qq[1], ri), v = dw_mul(qq[2], ri);
-        dw_acc A = dw_dot_begin(u, u);
-        dw_dot_add(A, v, v);
-        const dw K = dw_scale2(dw_dot_end(A), 0.5f);
-        const dw p = dw_mul(gm1, dw_sub(qq[3], dw_mul(qq[0], K)));
+        dw H, ri, u, v, p, K;
+        dw_adj_prims(qq, gm1, H, ri, u, v, p, K);
         float2 *W = s_cell;
         stw(W, 0 * cap_c + i, qq[0]);
         stw(W, 1 * cap_c + i, qq[1]);
         stw(W, 2 * cap_c + i, qq[2]);
-        stw(W, 3 * cap_c + i, dw_add(qq[3], p));
+        stw(W, 3 * cap_c + i, H);
         stw(W, 4 * cap_c + i, ri);
         stw(W, 5 * cap_c + i, u);
         stw(W, 6 * cap_c + i, v);
@@ -213,8 +221,12 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
             h[k] = dw_scale2(fb[k], 0.5f);
         }
         dw_acc NX, NY;
-        flux_rev_dw(S, c1, nx, ny, h, gm1, qb1, NX, NY, true);
-        flux_rev_dw(S, c2, nx, ny, h, gm1, qb2, NX, NY, false);
+        auto side = [&](int c, dw qb[4], bool first) {
+            flux_rev_dw(ldw(S[0], c), ldw(S[1], c), ldw(S[2], c), ldw(S[3], c), ldw(S[4], c), ldw(S[5], c),
+                        ldw(S[6], c), ldw(S[7], c), ldw(S[8], c), nx, ny, h, gm1, qb, NX, NY, first);
+        };
+        side(c1, qb1, true);
+        side(c2, qb2, false);
         nbx = dw_dot_end(NX);
         nby = dw_dot_end(NY);
         const dw mu = dw_add_fast(ldw(S[9], c1), ldw(S[9], c2));
@@ -311,13 +323,107 @@ __global__ void __launch_bounds__(512, 2) adjoint_hier_dw(const mp_block_desc *_
     }
 }
 
+// Global colouring and atomics (Sec. 2.1) in the same arithmetic: one thread
+// per edge of [e0, e1) reads its two nodes and two cells from global memory,
+// forms the per-cell values and both sides' reverse sweeps as the staged
+// kernel does, and writes q_bar (4 per cell) and x_bar (2 per node) either
+// with two FP64 additions (GLOBAL: edges of one colour share no cell or
+// node) or with one FP64 atomicAdd of the nearest double (ATOMIC).
+template <bool SOA, bool ATOMIC>
+__global__ void __launch_bounds__(256) adjoint_direct_dw(int e0, int e1, const int32_t *__restrict__ e2n,
+                                                         const int32_t *__restrict__ e2c,
+                                                         const double *__restrict__ x, const double *__restrict__ q,
+                                                         const double *__restrict__ adt,
+                                                         const double *__restrict__ rbar, double *__restrict__ qbar,
+                                                         double *__restrict__ xbar, int64_t nnode, int64_t ncell,
+                                                         dw gm1, dw half_eps)
+{
+    mp_pdl_trigger();
+    const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    const int2 nab = reinterpret_cast<const int2 *>(e2n)[e];
+    const int2 cc = reinterpret_cast<const int2 *>(e2c)[e];
+    auto X = [&](int64_t g, int k) { return SOA ? x[k * nnode + g] : x[2 * g + k]; };
+    const dw nx = dw_from_double_int(X(nab.x, 1) - X(nab.y, 1));  // exact in FP64
+    const dw ny = dw_from_double_int(X(nab.y, 0) - X(nab.x, 0));
+    dw qq[2][4], fb[4], h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t j1 = SOA ? k * ncell + cc.x : 4 * (int64_t)cc.x + k;
+        const int64_t j2 = SOA ? k * ncell + cc.y : 4 * (int64_t)cc.y + k;
+        qq[0][k] = dw_from_double_int(q[j1]);
+        qq[1][k] = dw_from_double_int(q[j2]);
+        fb[k] = dw_add_fast(dw_from_double_int(rbar[j1]), dw_neg(dw_from_double_int(rbar[j2])));
+        h[k] = dw_scale2(fb[k], 0.5f);
+    }
+    dw qb[2][4];
+    dw_acc NX, NY;
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        dw H, ri, u, v, p, K;
+        dw_adj_prims(qq[sd], gm1, H, ri, u, v, p, K);
+        flux_rev_dw(qq[sd][0], qq[sd][1], qq[sd][2], H, ri, u, v, p, K, nx, ny, h, gm1, qb[sd], NX, NY, sd == 0);
+    }
+    const dw nbx = dw_dot_end(NX), nby = dw_dot_end(NY);
+    const dw mu = dw_add_fast(dw_mul(dw_from_double_int(adt[cc.x]), half_eps),
+                              dw_mul(dw_from_double_int(adt[cc.y]), half_eps));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const dw m = dw_mul(mu, fb[k]);
+        qb[0][k] = dw_add_fast(qb[0][k], m);
+        qb[1][k] = dw_add_fast(qb[1][k], dw_neg(m));
+    }
+    // n_x = y_a - y_b, n_y = x_b - x_a: node a gets (-n_y_bar, n_x_bar), node b the opposite
+    const dw xi[2][2] = {{dw_neg(nby), nbx}, {nby, dw_neg(nbx)}};
+    const int node[2] = {nab.x, nab.y}, cell[2] = {cc.x, cc.y};
+    if (!ATOMIC) mp_pdl_wait();  // q_bar, x_bar: read-add-written by the previous colour's launch
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double *t = qbar + (SOA ? k * ncell + cell[sd] : 4 * (int64_t)cell[sd] + k);
+            if (ATOMIC)
+                atomicAdd(t, f32_to_f64_int(qb[sd][k].hi) + f32_to_f64_int(qb[sd][k].lo));
+            else
+                *t = f64_add_dw(*t, qb[sd][k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            double *t = xbar + (SOA ? k * nnode + node[sd] : 2 * (int64_t)node[sd] + k);
+            if (ATOMIC)
+                atomicAdd(t, f32_to_f64_int(xi[sd][k].hi) + f32_to_f64_int(xi[sd][k].lo));
+            else
+                *t = f64_add_dw(*t, xi[sd][k]);
+        }
+    }
+}
+
 template <bool SOA>
 int adjoint_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt, const void *rbar, void *qbar,
                  void *xbar, double gam, double eps, cudaStream_t s)
 {
+    const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
+    const double g1 = gam - 1.0, he = 0.5 * eps;
+    const float g1h = (float)g1, heh = (float)he;
+    const dw gm1{g1h, (float)(g1 - (double)g1h)}, half_eps{heh, (float)(he - (double)heh)};
+    if (P->opts.coloring == MP_COLOR_GLOBAL || P->opts.coloring == MP_COLOR_ATOMIC) {
+        const bool atomic = P->opts.coloring == MP_COLOR_ATOMIC;
+        auto kern = atomic ? adjoint_direct_dw<SOA, true> : adjoint_direct_dw<SOA, false>;
+        bool overlap = false;  // global colours: overlapped like the staged launches
+        for (int c = 0; c < P->ncolors; ++c) {
+            const int e0 = P->color_offsets[c], e1 = P->color_offsets[c + 1];
+            if (e1 <= e0) continue;
+            MP_CUDA_TRY(mp_launch(kern, (e1 - e0 + 255) / 256, 256, 0, s, overlap && !atomic, e0, e1,
+                                  P->dev.map[0], P->dev.map[1], (const double *)x, (const double *)q,
+                                  (const double *)adt, (const double *)rbar, (double *)qbar, (double *)xbar, nnode,
+                                  ncell, gm1, half_eps));
+            overlap = true;
+        }
+        MP_CUDA_TRY(cudaGetLastError());
+        return MP_OK;
+    }
     if (P->opts.coloring != MP_COLOR_HIER || P->maps[0].slot != 0 || P->maps[1].slot != 1) return MP_EPLAN;
     if (P->opts.block_size > 512) return MP_EINVAL;
-    const int64_t nnode = P->maps[0].to_size, ncell = P->maps[1].to_size;
     const int cap_n = P->stats.footprint_max[0], cap_c = P->stats.footprint_max[1];
     const bool gather = mp_staged(P, MP_STAGED_GATHER) == MP_STAGED_GATHER && mp_gather_ready(P);
     const int gw4 = gather ? P->gat_w / 4 : 0, cap_f = gather ? P->opts.block_size : 0;
@@ -331,9 +437,6 @@ int adjoint_dw_t(const mp_plan *P, const void *x, const void *q, const void *adt
     if (rc != MP_OK) return rc;
     int *err = nullptr;
     if ((rc = mp_device_error_word(&err)) != MP_OK) return rc;
-    const double g1 = gam - 1.0, he = 0.5 * eps;
-    const float g1h = (float)g1, heh = (float)he;
-    const dw gm1{g1h, (float)(g1 - (double)g1h)}, half_eps{heh, (float)(he - (double)heh)};
     bool overlap = false;
     for (int c = 0; c < P->ncolors; ++c) {
         const int b0 = P->color_offsets[c], nb = P->color_offsets[c + 1] - b0;

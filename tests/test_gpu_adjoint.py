@@ -140,6 +140,18 @@ def test_adjoint_double_word_parity(reorder, block_size, layout):
             assert np.array_equal(qb, qb2) and np.array_equal(xb, xb2)
 
 
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("coloring,reorder", [("global", "rcm"), ("atomic", "rcm"), ("atomic", "none")])
+def test_adjoint_double_word_baselines(coloring, reorder, layout):
+    """Global colouring and atomics (Sec. 2.1) in double-word arithmetic on
+    FP64 data: within the FP64 bar, like the two-layer form."""
+    m, q, adt, rb, P = setup(200, 100, coloring, reorder, layout)
+    qr, xr = oracle.res_calc_adjoint(m.edge2node, m.edge2cell, m.x, q, adt, rb)
+    qb, xb = gpu_adjoint(m, q, adt, rb, P, compute="dw")
+    assert rel_l2(qb, qr) <= 1e-12
+    assert rel_l2(xb, xr) <= 1e-12
+
+
 @pytest.mark.slow
 def test_adjoint_full_size():
     """The adjoint workload, 1200x600 quads, native FP64 and double-word."""
