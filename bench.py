@@ -691,7 +691,7 @@ def bench_adjoint(ml, torch, timer, args):
     rb = meshgen.adjoint_seed(am.ncell)
     for coloring, reorder, comp, staged, bs in (("hier", "partition", None, "gather", ADJ_BLOCK),
                                                 ("hier", "partition", None, "simple", 384),
-                                                ("hier", "partition", "dw", "gather", 256),
+                                                ("hier", "partition", "dw", "gather", 192),
                                                 ("hier", "partition", "dw", "simple", 256),
                                                 ("atomic", "rcm", None, None, 256), ("global", "rcm", None, None, 256),
                                                 ("atomic", "rcm", "dw", None, 256), ("global", "rcm", "dw", None, 256)):
