@@ -397,6 +397,9 @@ __global__ void __maxnreg__(64) adjoint_hier_g(adj_g_args<T> A, int block0)
                 const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    // padding (the zero row) comes last in a row, and halo
+                    // cells after interior ones: their warps skip it whole
+                    if (sizeof(T) == 8 && !__any_sync(__activemask(), es[j] != 2 * S)) continue;
                     T v0, v1, v2, v3;
                     ld_row4(s_eq, es[j], v0, v1, v2, v3);
                     a0 += v0;
@@ -415,6 +418,7 @@ __global__ void __maxnreg__(64) adjoint_hier_g(adj_g_args<T> A, int block0)
                 const unsigned short es[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    if (sizeof(T) == 8 && !__any_sync(__activemask(), es[j] != S)) continue;
                     const T sg = (es[j] & 0x8000u) ? T(-1) : T(1);
                     T v0, v1;
                     ld_row2(s_en, es[j] & 0x7fff, v0, v1);
